@@ -1,0 +1,356 @@
+"""Pins of the FP64 oracle to what the paper and the mathematics fix (CPU only).
+
+Each test checks the oracle against something other than itself: closed forms derived
+from the paper's definitions (tests/golden), a library routine that a special case
+reduces to, brute force from a definition, or an identity/theorem the paper proves.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.fft
+
+from oracle import definitions as D
+from oracle import lt_oracle as O
+from tests.conftest import load_golden_matrices, rel
+
+
+def rand(rng, *shape):
+    return rng.standard_normal(size=shape)
+
+
+def rand_invertible(rng, n, cond=10.0):
+    Q1, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    d = np.geomspace(1.0, cond, n)
+    return (Q1 * d) @ Q2.T
+
+
+# ---------------------------------------------------------------- transform matrices
+def test_dct_matrix_closed_forms_and_scipy():
+    g = load_golden_matrices()
+    for n in (2, 3):
+        assert np.allclose(O.dct_matrix(n), g[("dct", n)], atol=1e-15)
+    # Special case that reduces to a library routine: C_n x == DCT-II (orthonormal).
+    rng = np.random.default_rng(1)
+    for n in (1, 2, 3, 5, 8, 32, 33):
+        x = rng.standard_normal(n)
+        assert np.allclose(O.dct_matrix(n) @ x, scipy.fft.dct(x, type=2, norm="ortho"),
+                           atol=1e-14)
+        C = O.dct_matrix(n)
+        assert np.allclose(C @ C.T, np.eye(n), atol=1e-14)  # "C_n is orthogonal" (Sec. 2)
+
+
+def test_cproduct_matrix_closed_forms():
+    g = load_golden_matrices()
+    for n in (2, 3):
+        assert np.allclose(O.cproduct_matrix(n), g[("cprod", n)], atol=1e-14)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 7])
+def test_tph_diagonalisation_eq_d(n):
+    """Eq. (d): C tph(a) C^T = diag(d), d = W^{-1} C (I+Z) vec(a)."""
+    rng = np.random.default_rng(n)
+    a = rng.standard_normal(n)
+    T = D.btph(a.reshape(1, 1, n))
+    C = O.dct_matrix(n)
+    Dm = C @ T @ C.T
+    assert np.abs(Dm - np.diag(np.diag(Dm))).max() < 1e-13
+    assert np.allclose(np.diag(Dm), O.cproduct_matrix(n) @ a, atol=1e-13)
+
+
+# ---------------------------------------------------------------- mode products
+@pytest.mark.parametrize("shape", [(3, 4, 2), (2, 3, 4, 2), (2, 2, 3, 2, 3)])
+def test_mode_product_matricization(shape):
+    """Y = X x_n U  <=>  Y_(n) = U X_(n) (Sec. 2), with X_(n) built element by element."""
+    rng = np.random.default_rng(len(shape))
+    X = rand(rng, *shape)
+    for n in range(1, len(shape) + 1):
+        U = rand(rng, 5, shape[n - 1])
+        Y = O.mode_product(X, U, n)
+        assert Y.shape[n - 1] == 5
+        assert np.allclose(D.matricize(Y, n), U @ D.matricize(X, n), atol=1e-13)
+
+
+def test_matricization_third_order_examples():
+    """X_(1) = [X^(1), ..., X^(I3)] and X_(2) = [X^(1)T, ..., X^(I3)T] (Sec. 2)."""
+    rng = np.random.default_rng(3)
+    X = rand(rng, 3, 4, 2)
+    assert np.allclose(D.matricize(X, 1), np.hstack([X[:, :, i] for i in range(2)]))
+    assert np.allclose(D.matricize(X, 2), np.hstack([X[:, :, i].T for i in range(2)]))
+
+
+def test_mode_products_commute():
+    rng = np.random.default_rng(4)
+    X = rand(rng, 2, 3, 4, 5)
+    U, V = rand(rng, 4, 4), rand(rng, 5, 5)
+    a = O.mode_product(O.mode_product(X, U, 3), V, 4)
+    b = O.mode_product(O.mode_product(X, V, 4), U, 3)
+    assert np.allclose(a, b, atol=1e-13)
+
+
+@pytest.mark.parametrize("trailing", [(4,), (3, 2), (2, 3, 2)])
+def test_transform_kronecker_brute_force(trailing):
+    """vec(L(X)) = (M_K kron ... kron M_3 kron I) vec(X) and the round trip L^{-1}(L(X))."""
+    rng = np.random.default_rng(sum(trailing))
+    X = rand(rng, 3, 2, *trailing)
+    Ms = [rand_invertible(rng, n) for n in trailing]
+    Lx = O.transform(X, Ms)
+    assert rel(Lx, D.kron_transform(X, Ms)) < 1e-13
+    assert rel(O.inverse_transform(Lx, Ms), X) < 1e-12
+
+
+# ---------------------------------------------------------------- products
+@pytest.mark.parametrize("shapes", [((3, 2, 4), (2, 3, 4)), ((2, 3, 3, 2), (3, 2, 3, 2)),
+                                    ((2, 2, 2, 3, 2), (2, 1, 2, 3, 2))])
+def test_lemma_cproduct_equals_L_product(shapes):
+    """Lemma of Sec. 3.1: A *_c B = ten(btph(A) btph(B)) equals L^{-1}(L(A) tri L(B))
+    with M = W^{-1} C (I+Z) on every mode; plus btph(A *_c B) = btph(A) btph(B)."""
+    rng = np.random.default_rng(7)
+    A, B = rand(rng, *shapes[0]), rand(rng, *shapes[1])
+    Ms = [O.cproduct_matrix(n) for n in shapes[0][2:]]
+    C = O.product(A, B, Ms)
+    assert rel(C, D.cproduct_def(A, B)) < 1e-12
+    assert rel(D.btph(C), D.btph(A) @ D.btph(B)) < 1e-12
+    assert rel(D.ten(D.btph(A), A.shape), A) < 1e-15
+
+
+def test_dct_product_is_not_the_btph_cproduct():
+    """With the orthonormal C instead of M_c the product differs (the reason the two
+    transform kinds are kept apart)."""
+    rng = np.random.default_rng(8)
+    A, B = rand(rng, 3, 2, 4), rand(rng, 2, 3, 4)
+    assert rel(O.product(A, B, [O.dct_matrix(4)]), D.cproduct_def(A, B)) > 1e-3
+
+
+def test_slice_order_eq_3_5():
+    """Representative matrices X^p with p = k3 + I3 k4 + I3 I4 k5 (Eq. 3.5, mode 3
+    fastest), and the slices' round trip."""
+    rng = np.random.default_rng(5)
+    X = rand(rng, 2, 3, 3, 2, 2)
+    S = O.slices(X)
+    for k5 in range(2):
+        for k4 in range(2):
+            for k3 in range(3):
+                assert np.array_equal(S[:, :, k3 + 3 * k4 + 6 * k5], X[:, :, k3, k4, k5])
+    assert np.array_equal(O.from_slices(S, X.shape[2:]), X)
+
+
+def test_facewise_product_brute_force():
+    """(A tri B)^p = A^p B^p computed entry by entry from Eq. 3.5's slice order."""
+    rng = np.random.default_rng(9)
+    A, B = rand(rng, 3, 4, 2, 3), rand(rng, 4, 2, 2, 3)
+    C = O.facewise(A, B)
+    for k4 in range(3):
+        for k3 in range(2):
+            for i in range(3):
+                for j in range(2):
+                    s = sum(A[i, l, k3, k4] * B[l, j, k3, k4] for l in range(4))
+                    assert abs(C[i, j, k3, k4] - s) < 1e-13
+
+
+@pytest.mark.parametrize("kind", ["dct", "general"])
+def test_ring_laws_identity_transpose(kind):
+    rng = np.random.default_rng(10)
+    trailing = (3, 4)
+    Ms = ([O.dct_matrix(n) for n in trailing] if kind == "dct"
+          else [rand_invertible(rng, n) for n in trailing])
+    A, B, C = rand(rng, 3, 4, *trailing), rand(rng, 4, 2, *trailing), rand(rng, 2, 5, *trailing)
+    # identity (Sec. 3.2): A * I = I * A = A
+    assert rel(O.product(A, O.identity(4, trailing, Ms), Ms), A) < 1e-12
+    assert rel(O.product(O.identity(3, trailing, Ms), A, Ms), A) < 1e-12
+    # associativity and distributivity (ring theorem of Sec. 3.2)
+    assert rel(O.product(O.product(A, B, Ms), C, Ms), O.product(A, O.product(B, C, Ms), Ms)) < 1e-12
+    B2 = rand(rng, 4, 2, *trailing)
+    assert rel(O.product(A, B + B2, Ms), O.product(A, B, Ms) + O.product(A, B2, Ms)) < 1e-12
+    # commutativity of scalar-tensors
+    a, b = rand(rng, 1, 1, *trailing), rand(rng, 1, 1, *trailing)
+    assert rel(O.product(a, b, Ms), O.product(b, a, Ms)) < 1e-12
+    # transpose reversal (A * B)^T = B^T * A^T
+    lhs = O.transpose(O.product(A, B, Ms), Ms)
+    rhs = O.product(O.transpose(B, Ms), O.transpose(A, Ms), Ms)
+    assert rel(lhs, rhs) < 1e-12
+    # for transforms on modes >= 3 the transpose is the swap of modes 1 and 2
+    assert rel(O.transpose(A, Ms), np.swapaxes(A, 0, 1)) < 1e-12
+
+
+def test_scalar_tensor_expansion_and_column_split():
+    """Propositions of Sec. 3.2: (X * Y)_{ij} = sum_k X_{ik} * Y_{kj} (scalar-tensors),
+    and A * B = [A * B_1, ..., A * B_{I2}]."""
+    rng = np.random.default_rng(11)
+    trailing = (3, 2)
+    Ms = [rand_invertible(rng, n) for n in trailing]
+    X, Y = rand(rng, 2, 3, *trailing), rand(rng, 3, 2, *trailing)
+    XY = O.product(X, Y, Ms)
+    for i in range(2):
+        for j in range(2):
+            acc = sum(O.product(X[i:i + 1, k:k + 1], Y[k:k + 1, j:j + 1], Ms) for k in range(3))
+            assert rel(XY[i:i + 1, j:j + 1], acc) < 1e-12
+    cols = np.concatenate([O.product(X, Y[:, j:j + 1], Ms) for j in range(2)], axis=1)
+    assert rel(XY, cols) < 1e-12
+
+
+# ---------------------------------------------------------------- SVD / SVT
+@pytest.mark.parametrize("kind,shape", [("dct", (7, 5, 4)), ("dct", (4, 6, 3, 2)),
+                                        ("general", (6, 6, 2, 3))])
+def test_svd_invariants(kind, shape):
+    """Theorem of Eq. tsvd1: A = U * S * V^T with U, V orthogonal (every L(U)^p, L(V)^p
+    orthogonal), S f-diagonal; sigma >= 0 descending; for orthonormal L, ||A|| = ||S||
+    and ||S_1|| >= ||S_2|| >= ... (Corollary of Sec. 3.2)."""
+    rng = np.random.default_rng(12)
+    A = rand(rng, *shape)
+    trailing = shape[2:]
+    Ms = ([O.dct_matrix(n) for n in trailing] if kind == "dct"
+          else [rand_invertible(rng, n) for n in trailing])
+    U, S, V, sig = O.svd(A, Ms)
+    rec = O.product(O.product(U, S, Ms), O.transpose(V, Ms), Ms)
+    assert rel(rec, A) < 1e-12
+    Uh, Sh, Vh = (O.slices(O.transform(T, Ms)) for T in (U, S, V))
+    for p in range(Uh.shape[2]):
+        assert np.allclose(Uh[:, :, p].T @ Uh[:, :, p], np.eye(shape[0]), atol=1e-12)
+        assert np.allclose(Vh[:, :, p].T @ Vh[:, :, p], np.eye(shape[1]), atol=1e-12)
+        off = Sh[:, :, p].copy()
+        np.fill_diagonal(off, 0.0)
+        assert np.abs(off).max() < 1e-12
+        s = np.diag(Sh[:, :, p])
+        assert np.all(s >= -1e-13) and np.all(np.diff(s) <= 1e-13)
+        # sigma equals the singular values of L(A)^p (brute: eigenvalues of the Gram)
+        ev = np.sqrt(np.maximum(np.linalg.eigvalsh(
+            O.slices(O.transform(A, Ms))[:, :, p].T @ O.slices(O.transform(A, Ms))[:, :, p]), 0))
+        assert np.allclose(np.sort(ev)[::-1][: len(s)], s, atol=1e-10)
+    # Q * Q^T = I (orthogonal tensor definition)
+    I1 = shape[0]
+    assert rel(O.product(U, O.transpose(U, Ms), Ms), O.identity(I1, trailing, Ms)) < 1e-12
+    if kind == "dct":
+        assert abs(np.linalg.norm(A) - np.linalg.norm(S)) < 1e-12 * np.linalg.norm(A)
+        r = min(shape[:2])
+        norms = [np.linalg.norm(S[i, i]) for i in range(r)]
+        assert all(norms[i] >= norms[i + 1] - 1e-12 for i in range(r - 1))
+        assert abs(sum(x * x for x in norms) - np.linalg.norm(A) ** 2) < 1e-10
+
+
+def test_eckart_young_dct():
+    """Eckart-Young theorem of Sec. 3.2: ||A - A_k||^2 = sum_{i>k} ||S_i||^2 (orthonormal
+    L), and A_k beats other rank-k products."""
+    rng = np.random.default_rng(13)
+    trailing = (3, 2)
+    Ms = [O.dct_matrix(n) for n in trailing]
+    A = rand(rng, 6, 5, *trailing)
+    U, S, V, _ = O.svd(A, Ms)
+    for k in range(1, 5):
+        Ak = O.product(O.product(U[:, :k], S[:k, :k], Ms), O.transpose(V[:, :k], Ms), Ms)
+        err2 = np.linalg.norm(A - Ak) ** 2
+        tail = sum(np.linalg.norm(S[i, i]) ** 2 for i in range(k, 5))
+        assert abs(err2 - tail) < 1e-10 * np.linalg.norm(A) ** 2
+        X, Y = rand(rng, 6, k, *trailing), rand(rng, k, 5, *trailing)
+        assert np.linalg.norm(A - O.product(X, Y, Ms)) ** 2 >= err2 - 1e-10
+
+
+def test_svt_special_cases():
+    rng = np.random.default_rng(14)
+    trailing = (4,)
+    Ms = [rand_invertible(rng, 4)]
+    A = rand(rng, 5, 3, *trailing)
+    assert rel(O.svt(A, 0.0, Ms), A) < 1e-12            # tau = 0 gives A back
+    _, sig = O.svt(A, 0.0, Ms, return_sigma=True)
+    assert np.abs(O.svt(A, float(sig.max()) * 1.0001, Ms)).max() < 1e-13  # tau >= sigma_max
+    # I3 = 1 with M = [1]: the matrix SVT of Cai, Candes & Shen (via LAPACK)
+    M = rand(rng, 6, 4)
+    u, s, vt = np.linalg.svd(M, full_matrices=False)
+    ref = (u * np.maximum(s - 0.7, 0)) @ vt
+    assert rel(O.svt(M.reshape(6, 4, 1), 0.7, [np.eye(1)])[:, :, 0], ref) < 1e-13
+    # scaled identity transform alpha * I leaves the product structure but scales sigma
+    out = O.svt(M.reshape(6, 4, 1), 0.7, [np.array([[2.0]])])[:, :, 0]
+    ref2 = (u * np.maximum(2 * s - 0.7, 0) / 2.0) @ vt
+    assert rel(out, ref2) < 1e-13
+
+
+def test_svt_is_the_prox_of_the_nuclear_norm():
+    """Theorem 23 (orthonormal L): D_tau(A) minimises tau ||Y||_* + 1/2 ||Y - A||^2.
+    Checked against random perturbations and by the subgradient condition in each
+    transform-domain slice: A_hat - D_hat = tau (U1 V1^T + W) with ||W|| <= 1."""
+    rng = np.random.default_rng(15)
+    trailing = (3, 2)
+    Ms = [O.dct_matrix(n) for n in trailing]
+    A = rand(rng, 5, 4, *trailing)
+    tau = 0.8
+    Dt = O.svt(A, tau, Ms)
+
+    def F(Y):
+        return tau * O.nuclear_norm(Y, Ms) + 0.5 * np.linalg.norm(Y - A) ** 2
+
+    f0 = F(Dt)
+    for _ in range(200):
+        P = rand(rng, *A.shape) * 10 ** rng.uniform(-4, 0)
+        assert F(Dt + P) >= f0 - 1e-12
+    Ah, Dh = O.slices(O.transform(A, Ms)), O.slices(O.transform(Dt, Ms))
+    for p in range(Ah.shape[2]):
+        Gp = (Ah[:, :, p] - Dh[:, :, p]) / tau
+        assert np.linalg.norm(Gp, 2) <= 1 + 1e-10
+
+
+# ---------------------------------------------------------------- PGA (Algorithm 5)
+def small_completion(seed=16, I1=8, I2=7, trailing=(3, 4), rank=2, rho=0.5):
+    rng = np.random.default_rng(seed)
+    Ms = [O.dct_matrix(n) for n in trailing]
+    U, V = rand(rng, I1, rank, *trailing), rand(rng, I2, rank, *trailing)
+    X = O.product(U, O.transpose(V, Ms), Ms)
+    mask = (rng.random(X.shape) < rho).astype(np.uint8)
+    obs = mask * X
+    return X, mask, obs, Ms
+
+
+def test_pga_full_observation_reduces_to_one_svt():
+    """Omega = everything and step = 1: G^k = M for every k (Eq. 51), so every iterate
+    is D_tau(M) (Eq. 53) whatever the momentum."""
+    X, mask, obs, Ms = small_completion()
+    ones = np.ones_like(mask)
+    Xk, info = O.pga(ones, X, 0.3, 1.0, 5, Ms)
+    assert rel(Xk, O.svt(X, 0.3, Ms)) < 1e-13
+    assert info["iters"] == 5
+
+
+def test_pga_first_iterates_and_momentum_schedule():
+    """With t_0 = t_1 = 1 the first two momentum weights vanish, so X^2 = D(P(M)) and
+    X^3 = D(X^2 - P(X^2 - M)); the third weight is (t_2 - 1)/t_3 with t_2 the golden
+    ratio (FISTA schedule t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2)."""
+    X, mask, obs, Ms = small_completion()
+    tau = 0.2
+    m = mask.astype(float)
+    x2 = O.svt(m * obs, tau, Ms)
+    x3 = O.svt(x2 - m * (x2 - obs), tau, Ms)
+    got2, _ = O.pga(mask, obs, tau, 1.0, 1, Ms)
+    got3, info = O.pga(mask, obs, tau, 1.0, 2, Ms)
+    assert rel(got2, x2) < 1e-14 and rel(got3, x3) < 1e-14
+    phi = (1 + math.sqrt(5)) / 2
+    assert abs(info["t"] - (1 + math.sqrt(1 + 4 * phi * phi)) / 2) < 1e-15
+    y4 = x3 + (phi - 1) / info["t"] * (x3 - x2)
+    got4, _ = O.pga(mask, obs, tau, 1.0, 3, Ms)
+    assert rel(got4, O.svt(y4 - m * (y4 - obs), tau, Ms)) < 1e-13
+
+
+def test_pga_ista_monotone_and_limit_is_optimal():
+    """Without momentum the objective F = tau||X||_* + 1/2||P(X - M)||^2 never increases
+    (proximal gradient with step 1 = 1/l_f, Sec. 4), FISTA converges to the same
+    minimiser, and the limit beats random perturbations (convex optimality)."""
+    X, mask, obs, Ms = small_completion(rho=0.6)
+    tau = 0.05
+    _, info = O.pga(mask, obs, tau, 1.0, 60, Ms, momentum=False, objective=True)
+    f = info["objective"]
+    assert all(f[i + 1] <= f[i] + 1e-12 for i in range(len(f) - 1))
+    Xf, infof = O.pga(mask, obs, tau, 1.0, 400, Ms, objective=True)
+    Fstar = infof["objective"][-1]
+    rng = np.random.default_rng(0)
+    for _ in range(100):
+        P = rng.standard_normal(X.shape) * 10 ** rng.uniform(-4, -1)
+        assert O.pga_objective(Xf + P, mask, obs, tau, Ms) >= Fstar - 1e-9
+    # Beck-Teboulle rate for FISTA: F(X^k) - F* <= 2 ||X^0 - X*||^2 / (k+1)^2
+    for k, fk in enumerate(infof["objective"][:100], start=1):
+        assert fk - Fstar <= 2 * np.linalg.norm(Xf) ** 2 / (k + 1) ** 2 + 1e-9
+
+
+def test_pga_tolerance_stop_and_recovery():
+    X, mask, obs, Ms = small_completion(I1=12, I2=10, rank=1, rho=0.7)
+    Xk, info = O.pga(mask, obs, 0.01, 1.0, 500, Ms, tol=1e-6)
+    assert info["iters"] < 500 and info["residual"][-1] <= 1e-6
+    assert O.rse(X, Xk) < 0.05
