@@ -1,0 +1,227 @@
+/*
+ * lt.h -- C ABI of liblt, a GB300 (sm_103a) library for the generalized *_L-product,
+ * *_L-SVD, *_L-SVT and PGA tensor completion of Bentbib, Elalj, El Hachimi, Jbilou and
+ * Ratnani, "Generalized L-product for high order tensors with applications using GPU
+ * computations" (arXiv 2202.02870).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Tensors.  A K-th order tensor X in R^{I1 x I2 x I3 x ... x IK} (K >= 3) is a dense
+ *   buffer in column-major order, mode 1 fastest: element (i1, ..., iK) (0-based) sits
+ *   at i1 + I1*(i2 + I2*(i3 + I3*(...))).  The p-th frontal slice ("representative
+ *   matrix" X^p, Eq. 3.5) is therefore the contiguous column-major I1 x I2 block at
+ *   offset p*I1*I2, p = k3 + I3*k4 + I3*I4*k5 + ...  In torch this is a contiguous
+ *   tensor of shape (IK, ..., I3, I2, I1).
+ * Element type.  double for LT_FP64 contexts, float for LT_FP32 and LT_MIXED contexts.
+ * Pointers.  Tensor arguments are DEVICE pointers owned by the caller; the library
+ *   never frees or retains them after the call's work completes.  Host arguments are
+ *   marked "host".
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Every compute call only enqueues work on it and returns; results are valid after
+ *   the stream is synchronised.
+ * Workspace.  Calls that need scratch take `ws`, a caller-owned device buffer of at
+ *   least `ws_bytes` >= lt_workspace_size(...) bytes, 256-byte aligned.  It must not
+ *   be used by anything else until the call's work has completed on `stream`.
+ * Errors.  A return value other than LT_OK means that nothing was enqueued (argument,
+ *   shape, workspace and launch-configuration errors are detected on the host).
+ *   Errors found while kernels run (Jacobi not converged, non-finite values, an
+ *   expired bounded wait) are OR-ed into a per-context device status word, read with
+ *   lt_last_device_status() after synchronisation; outputs are still written.
+ * Threads.  A context may be used from one host thread at a time.
+ */
+#ifndef LT_H_
+#define LT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(_WIN32)
+#define LT_API __declspec(dllexport)
+#else
+#define LT_API __attribute__((visibility("default")))
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LT_OK = 0,
+  LT_ERR_ARG = -1,        /* null pointer, negative size, bad option, tau < 0, ... */
+  LT_ERR_SHAPE = -2,      /* sizes outside what the kernels support */
+  LT_ERR_SINGULAR = -3,   /* a transform matrix is singular or too ill-conditioned */
+  LT_ERR_NOCONV = -4,     /* (device) Jacobi hit max_sweeps before converging */
+  LT_ERR_TIMEOUT = -5,    /* (device) a bounded wait expired */
+  LT_ERR_NONFINITE = -6,  /* (device) NaN or Inf met in a slice */
+  LT_ERR_CUDA = -7,       /* a CUDA runtime call failed */
+  LT_ERR_WORKSPACE = -8   /* ws missing, too small or misaligned */
+} lt_status;
+
+/* Bits of the device status word (lt_last_device_status). */
+#define LT_DEV_NOCONV 0x1
+#define LT_DEV_NONFINITE 0x2
+#define LT_DEV_TIMEOUT 0x4
+
+typedef enum {
+  LT_FP64 = 0,  /* every step in IEEE double */
+  LT_FP32 = 1,  /* every step in IEEE single (SIMT) */
+  LT_MIXED = 2  /* float data; transforms and face-wise GEMMs on the tcgen05 tensor
+                   cores as split TF32 x 3 products with FP32 accumulation; Jacobi in
+                   FP32; reductions of the PGA residual in FP64 */
+} lt_precision;
+
+typedef enum {
+  LT_OP_TRANSFORM = 0,
+  LT_OP_INVERSE = 1,
+  LT_OP_PRODUCT = 2,
+  LT_OP_SVD = 3,
+  LT_OP_SVT = 4,
+  LT_OP_PGA = 5
+} lt_op;
+
+typedef enum {
+  LT_OPT_MAX_SWEEPS = 0,     /* Jacobi sweep limit (default 40); NOCONV when hit */
+  LT_OPT_JACOBI_TOL = 1,     /* pair tolerance: rotate when |a.b| > tol*sqrt(a.a b.b);
+                                value <= 0 restores the default (m * unit roundoff for
+                                LT_FP64, 4 * sqrt(m) * unit roundoff otherwise) */
+  LT_OPT_OBJECTIVE = 2       /* PGA: also accumulate the objective (0/1, default 0) */
+} lt_option;
+
+typedef struct lt_ctx_s* lt_ctx;
+
+/* ---------------------------------------------------------------------------------
+ * Transform matrices (host helpers; no GPU needed).
+ * ------------------------------------------------------------------------------- */
+
+/* Orthonormal DCT-II matrix C_n of Sec. 2 (the matrix C under Eq. (m); "M_i = C_i" in
+ * the experiments of Sec. 5), read with delta_{i,1}:
+ *   C[i][j] = sqrt((2 - delta_{i,0}) / n) cos(i (2j+1) pi / (2n)),  0 <= i, j < n.
+ * M: host, n*n doubles, written ROW-major (M[i*n + j] = C_{ij}).
+ * Errors: LT_ERR_ARG if n < 1 or M == NULL. */
+LT_API lt_status lt_make_dct(int64_t n, double* M);
+
+/* c-product transform of Eq. (m): M = W^{-1} C (I + Z), W = diag(C(:,1)),
+ * Z = superdiagonal ones.  With it on every mode the *_L-product is the generalized
+ * c-product ten(btph(A) btph(B)) (Lemma of Sec. 3.1).  Same layout and errors as
+ * lt_make_dct. */
+LT_API lt_status lt_make_cproduct(int64_t n, double* M);
+
+/* ---------------------------------------------------------------------------------
+ * Context: the operator L of Sec. 3.2, L(A) = A x_3 M_3 x_4 ... x_K M_K.
+ * ------------------------------------------------------------------------------- */
+
+/* K: tensor order, 3 <= K <= 10.  mode_sizes: host, K-2 entries I3..IK (each >= 1,
+ * product P <= 2^31 - 1).  M: host array of K-2 host pointers; M[k] is the
+ * I_{k+3} x I_{k+3} matrix M_{k+3}, ROW-major doubles.  The inverses are computed on
+ * the host in FP64 (LU with partial pivoting; an orthogonal matrix is inverted
+ * exactly by its transpose).  The context owns device copies of M_k and M_k^{-1} (in
+ * the context's precision) and a small status block; it owns no data buffers.
+ * Errors: LT_ERR_ARG, LT_ERR_SINGULAR (zero pivot or estimated 1-norm condition
+ * number > 1e12), LT_ERR_CUDA.  Needs a current CUDA device. */
+LT_API lt_status lt_ctx_create(int K, const int64_t* mode_sizes, const double* const* M,
+                        lt_precision prec, lt_ctx* out);
+LT_API lt_status lt_ctx_destroy(lt_ctx ctx);
+LT_API lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value);
+
+/* Bytes of workspace that `op` needs for slices of I1 x I2 (for LT_OP_PRODUCT:
+ * A is I1 x I2 and B is I2 x I2b; otherwise I2b is ignored).  out: host. */
+LT_API lt_status lt_workspace_size(lt_ctx ctx, lt_op op, int64_t I1, int64_t I2, int64_t I2b,
+                            size_t* out);
+
+/* ---------------------------------------------------------------------------------
+ * Operations.  Device pointers, column-major (see top of file).
+ * ------------------------------------------------------------------------------- */
+
+/* X_hat = L(X) = X x_3 M_3 ... x_K M_K (Sec. 3.2).  X, X_hat: I1*I2*P elements; may
+ * alias (in place). */
+LT_API lt_status lt_transform(lt_ctx ctx, int64_t I1, int64_t I2, const void* X, void* X_hat,
+                       void* ws, size_t ws_bytes, void* stream);
+
+/* X = L^{-1}(X_hat) = X_hat x_K M_K^{-1} ... x_3 M_3^{-1} (Sec. 3.2). */
+LT_API lt_status lt_inverse(lt_ctx ctx, int64_t I1, int64_t I2, const void* X_hat, void* X,
+                     void* ws, size_t ws_bytes, void* stream);
+
+/* C = A *_L B = L^{-1}(L(A) tri L(B)), Algorithm 2 (Def. of Sec. 3.2): A is
+ * I1 x l x I3..IK, B is l x I2 x I3..IK, C is I1 x I2 x I3..IK.  C must not alias
+ * A or B. */
+LT_API lt_status lt_product(lt_ctx ctx, int64_t I1, int64_t l, int64_t I2, const void* A,
+                     const void* B, void* C, void* ws, size_t ws_bytes, void* stream);
+
+/* *_L-SVD, Algorithm 3 (Theorem of Eq. tsvd1): A = U *_L S *_L V^T with U
+ * (I1 x I1 x ...), S (I1 x I2 x ...), V (I2 x I2 x ...); every L(U)^p, L(V)^p is
+ * orthogonal and L(S)^p = diag(sigma^p), sigma^p descending.  Singular vectors of
+ * repeated or zero singular values (and the completion of U or V to a square basis)
+ * are not unique.  sigma: optional device buffer of min(I1,I2)*P elements receiving
+ * the per-slice singular values (slice-major), may be NULL. */
+LT_API lt_status lt_svd(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, void* U, void* S,
+                 void* V, void* sigma, void* ws, size_t ws_bytes, void* stream);
+
+/* *_L-SVT D_tau(A), Algorithm 4 (Def. of D_tau, Theorem 23): per transform-domain
+ * slice, singular values shrunk to max(sigma - tau, 0), threshold tau applied
+ * unscaled in the transform domain.  tau >= 0.  D may alias A. */
+LT_API lt_status lt_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau, void* D,
+                 void* ws, size_t ws_bytes, void* stream);
+
+/* Checkpoint of a PGA run (Algorithm 5): X^{k-1} (caller-owned device buffer of the
+ * problem's size), t_{k-1}, t_k and k.  With k == 0 the run starts from X^0 = X^1 =
+ * the X argument and t_0 = t_1 = 1. */
+typedef struct {
+  void* X_prev;
+  double t_prev;
+  double t;
+  int64_t k;
+} lt_pga_state;
+
+typedef struct {
+  int64_t iters_done;     /* iterations performed by this call */
+  double rel_residual;    /* ||Y^k - X^{k+1}||_F / ||X^{k+1}||_F of the last one */
+  double objective;       /* tau*sum_p ||L(X)^p||_* + 1/2 ||P_Omega(X - M)||^2, if
+                             LT_OPT_OBJECTIVE is on, else 0 */
+  int32_t max_sweeps_used;
+  int32_t device_status;  /* LT_DEV_* bits raised during the call */
+} lt_pga_report;
+
+/* Tensor completion by PGA, Algorithm 5 with the Eqs. 50-53 steps and a fixed
+ * threshold (no mu continuation):
+ *   Y = X^k + ((t_{k-1} - 1)/t_k)(X^k - X^{k-1})            (Eq. 52)
+ *   G = Y - step * P_Omega(Y - M)                            (Eq. 51, l_f = 1/step)
+ *   X^{k+1} = D_{step*tau}(G)                                (Eq. 53, Algorithm 4)
+ *   t_{k+1} = (1 + sqrt(4 t_k^2 + 1)) / 2
+ *   r_k = ||Y - X^{k+1}||_F / ||X^{k+1}||_F                  (stopping test of Sec. 5)
+ * for `iters` iterations, or fewer when tol > 0 and r_k <= tol.
+ * mask: device uint8, I1*I2*P, nonzero = observed (Omega).  obs: device, values of M
+ * (entries outside Omega are ignored).  X: device, in = start (X^k; zeros for a cold
+ * start), out = the last iterate X^{k+1}.  state: host, may be NULL (cold start and
+ * no checkpoint); if given, it is read at the call and, like `report` (host, may be
+ * NULL), written once the stream reaches the end of the call's work: both must stay
+ * valid until then.  state->X_prev must not alias X. */
+LT_API lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8_t* mask,
+                          const void* obs, double tau, double step, int64_t iters,
+                          double tol, void* X, lt_pga_state* state, lt_pga_report* report,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* Many independent completion problems (each with its own context, sizes, mask,
+ * observations, tau and step; all contexts of one precision) run together: each
+ * stage of an iteration is one launch over all problems' tiles or slices.  ws: one
+ * buffer of at least lt_workspace_size_batched bytes.  reports: host array of nprob
+ * (may be NULL), written when the stream reaches the end of the work. */
+LT_API lt_status lt_workspace_size_batched(int nprob, const lt_ctx* ctxs, const int64_t* I1,
+                                    const int64_t* I2, size_t* out);
+LT_API lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const int64_t* I1,
+                                  const int64_t* I2, const uint8_t* const* mask,
+                                  const void* const* obs, const double* tau,
+                                  const double* step, int64_t iters, void* const* X,
+                                  lt_pga_report* reports, void* ws, size_t ws_bytes,
+                                  void* stream);
+
+/* Device status word of the context: OR of LT_DEV_* bits raised since the previous
+ * call of this function (read and cleared).  Synchronises the device. out: host. */
+LT_API lt_status lt_last_device_status(lt_ctx ctx, int32_t* out);
+
+/* Static description of a status code. */
+LT_API const char* lt_status_string(lt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LT_H_ */

@@ -1,0 +1,568 @@
+// Host side of the liblt C ABI: argument checks, contexts (the operator L of Sec. 3.2
+// with its device-resident matrices), workspace layouts, and the orchestration of the
+// kernels for every call.  Nothing here computes on tensor data: every step of
+// every operation runs in the kernels of lt_transform.cu, lt_gemm.cu, lt_jacobi.cu and
+// lt_pga.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lt_internal.cuh"
+
+using lt::Ctx;
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+lt_status cuda_status(cudaError_t e) { return e == cudaSuccess ? LT_OK : LT_ERR_CUDA; }
+
+// ---- dense FP64 helpers on the host (transform set-up only) ------------------------
+// Inverse by Gaussian elimination with partial pivoting on [M | I]; row-major n x n.
+bool invert(const double* M, int64_t n, double* out, double* pivot_min) {
+  std::vector<double> a((size_t)n * 2 * n);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < 2 * n; ++j)
+      a[i * 2 * n + j] = j < n ? M[i * n + j] : (j - n == i ? 1.0 : 0.0);
+  double pmin = INFINITY;
+  for (int64_t col = 0; col < n; ++col) {
+    int64_t piv = col;
+    for (int64_t r = col + 1; r < n; ++r)
+      if (std::fabs(a[r * 2 * n + col]) > std::fabs(a[piv * 2 * n + col])) piv = r;
+    const double pv = a[piv * 2 * n + col];
+    pmin = std::min(pmin, std::fabs(pv));
+    if (pv == 0.0 || !std::isfinite(pv)) return false;
+    if (piv != col)
+      for (int64_t j = 0; j < 2 * n; ++j) std::swap(a[piv * 2 * n + j], a[col * 2 * n + j]);
+    const double inv = 1.0 / a[col * 2 * n + col];
+    for (int64_t j = 0; j < 2 * n; ++j) a[col * 2 * n + j] *= inv;
+    for (int64_t r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double f = a[r * 2 * n + col];
+      if (f == 0.0) continue;
+      for (int64_t j = 0; j < 2 * n; ++j) a[r * 2 * n + j] -= f * a[col * 2 * n + j];
+    }
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) out[i * n + j] = a[i * 2 * n + n + j];
+  *pivot_min = pmin;
+  return true;
+}
+
+double norm1(const double* M, int64_t n) {  // max column sum
+  double best = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; ++i) s += std::fabs(M[i * n + j]);
+    best = std::max(best, s);
+  }
+  return best;
+}
+
+bool is_orthogonal(const double* M, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int64_t k = 0; k < n; ++k) s += M[i * n + k] * M[j * n + k];
+      if (std::fabs(s - (i == j ? 1.0 : 0.0)) > 64 * 2.2e-16 * n) return false;
+    }
+  return true;
+}
+
+template <typename T>
+void convert(const std::vector<double>& src, std::vector<unsigned char>& dst) {
+  dst.resize(src.size() * sizeof(T));
+  T* d = reinterpret_cast<T*>(dst.data());
+  for (size_t i = 0; i < src.size(); ++i) d[i] = (T)src[i];
+}
+
+lt_status check_ctx(lt_ctx c) { return c == nullptr ? LT_ERR_ARG : LT_OK; }
+
+lt_status check_ws(void* ws, size_t have, size_t need) {
+  if (need == 0) return LT_OK;
+  if (ws == nullptr || have < need) return LT_ERR_WORKSPACE;
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0) return LT_ERR_WORKSPACE;
+  return LT_OK;
+}
+
+lt_status check_dims(int64_t a, int64_t b) {
+  if (a < 1 || b < 1) return LT_ERR_ARG;
+  if (a > (1 << 20) || b > (1 << 20)) return LT_ERR_SHAPE;
+  return LT_OK;
+}
+
+// ---- workspace layouts ---------------------------------------------------------------
+struct PgaLayout {
+  size_t x2, ghat, partials, scal, info, jac, total;
+  lt::TransformPlan fwd, inv;
+  lt::JacobiPlan jp;
+  int max_rows;
+};
+
+lt_status pga_layout(const Ctx& c, int64_t I1, int64_t I2, PgaLayout* L) {
+  const int64_t N = I1 * I2 * c.P;
+  lt_status s = lt::plan_transform(c, I1 * I2, false, &L->fwd);
+  if (s != LT_OK) return s;
+  s = lt::plan_transform(c, I1 * I2, true, &L->inv);
+  if (s != LT_OK) return s;
+  s = lt::plan_jacobi(c, lt::JAC_SVT, I1, I2, &L->jp);
+  if (s != LT_OK) return s;
+  L->max_rows = lt::transform_grid(c, L->inv.pass[L->inv.npass - 1]);
+  size_t off = 0;
+  L->x2 = off; off += align256((size_t)N * c.elem);
+  L->ghat = off; off += align256((size_t)N * c.elem);
+  L->partials = off; off += align256((size_t)L->max_rows * 4 * sizeof(double));
+  L->scal = off; off += align256(sizeof(lt::PgaScalars));
+  L->info = off; off += align256((size_t)c.P * sizeof(lt::SliceInfo));
+  L->jac = off; off += align256(L->jp.ws_bytes);
+  L->total = off;
+  return LT_OK;
+}
+
+struct ReportJob {
+  const lt::PgaScalars* pinned;
+  lt_pga_report* rep;
+  lt_pga_state* state;
+};
+
+void CUDART_CB report_cb(void* p) {
+  ReportJob* j = static_cast<ReportJob*>(p);
+  const lt::PgaScalars& s = *j->pinned;
+  if (j->rep) {
+    j->rep->iters_done = s.k_done;
+    j->rep->rel_residual = s.rel_residual;
+    j->rep->objective = s.objective;
+    j->rep->max_sweeps_used = s.max_sweeps_used;
+    j->rep->device_status = s.status;
+  }
+  if (j->state) {
+    j->state->t_prev = s.t_prev;
+    j->state->t = s.t;
+    j->state->k = s.k_total;
+  }
+  delete j;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lt_status_string(lt_status s) {
+  switch (s) {
+    case LT_OK: return "ok";
+    case LT_ERR_ARG: return "invalid argument";
+    case LT_ERR_SHAPE: return "unsupported shape";
+    case LT_ERR_SINGULAR: return "singular or ill-conditioned transform matrix";
+    case LT_ERR_NOCONV: return "Jacobi SVD did not converge within max_sweeps";
+    case LT_ERR_TIMEOUT: return "bounded device wait expired";
+    case LT_ERR_NONFINITE: return "non-finite value";
+    case LT_ERR_CUDA: return "CUDA runtime error";
+    case LT_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+  }
+  return "unknown status";
+}
+
+lt_status lt_make_dct(int64_t n, double* M) {
+  if (n < 1 || M == nullptr) return LT_ERR_ARG;
+  for (int64_t i = 0; i < n; ++i) {
+    const double scale = std::sqrt((i == 0 ? 1.0 : 2.0) / (double)n);
+    for (int64_t j = 0; j < n; ++j)
+      M[i * n + j] = scale * std::cos((double)i * (2.0 * j + 1.0) * kPi / (2.0 * n));
+  }
+  return LT_OK;
+}
+
+lt_status lt_make_cproduct(int64_t n, double* M) {
+  if (n < 1 || M == nullptr) return LT_ERR_ARG;
+  std::vector<double> C((size_t)n * n);
+  lt_make_dct(n, C.data());
+  // M = W^{-1} C (I + Z): column j of C(I+Z) is C(:, j) + C(:, j-1); row i scaled by
+  // 1 / C(i, 0).
+  for (int64_t i = 0; i < n; ++i) {
+    const double w = C[i * n + 0];
+    for (int64_t j = 0; j < n; ++j) {
+      const double v = C[i * n + j] + (j > 0 ? C[i * n + j - 1] : 0.0);
+      M[i * n + j] = v / w;
+    }
+  }
+  return LT_OK;
+}
+
+lt_status lt_ctx_create(int K, const int64_t* mode_sizes, const double* const* M,
+                        lt_precision prec, lt_ctx* out) {
+  if (out == nullptr) return LT_ERR_ARG;
+  *out = nullptr;
+  if (K < 3 || K - 2 > lt::kMaxModes || mode_sizes == nullptr || M == nullptr) return LT_ERR_ARG;
+  if (prec != LT_FP64 && prec != LT_FP32) return LT_ERR_ARG;
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) return LT_ERR_ARG;
+  c->K = K;
+  c->nmodes = K - 2;
+  c->prec = prec;
+  c->elem = prec == LT_FP64 ? 8 : 4;
+  int64_t P = 1;
+  std::vector<double> fwd, inv;
+  for (int q = 0; q < c->nmodes; ++q) {
+    const int64_t n = mode_sizes[q];
+    if (n < 1 || n > 4096 || M[q] == nullptr) { delete c; return LT_ERR_ARG; }
+    c->sizes[q] = n;
+    P *= n;
+    if (P > (int64_t)INT32_MAX) { delete c; return LT_ERR_SHAPE; }
+    c->mat_off[q] = (int64_t)fwd.size();
+    std::vector<double> Mi((size_t)n * n);
+    for (int64_t i = 0; i < n * n; ++i) {
+      if (!std::isfinite(M[q][i])) { delete c; return LT_ERR_ARG; }
+    }
+    if (is_orthogonal(M[q], n)) {  // inverse = transpose, exactly
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) Mi[i * n + j] = M[q][j * n + i];
+    } else {
+      double pmin = 0.0;
+      if (!invert(M[q], n, Mi.data(), &pmin)) { delete c; return LT_ERR_SINGULAR; }
+      const double cond = norm1(M[q], n) * norm1(Mi.data(), n);
+      if (!(cond <= 1e12)) { delete c; return LT_ERR_SINGULAR; }
+    }
+    fwd.insert(fwd.end(), M[q], M[q] + n * n);
+    inv.insert(inv.end(), Mi.begin(), Mi.end());
+  }
+  c->P = P;
+  cudaGetDevice(&c->device);
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device) == cudaSuccess && sms > 0)
+    c->sms = sms;
+  std::vector<unsigned char> bf, bi;
+  if (c->elem == 8) { convert<double>(fwd, bf); convert<double>(inv, bi); }
+  else { convert<float>(fwd, bf); convert<float>(inv, bi); }
+  cudaError_t e = cudaMalloc(&c->d_fwd, bf.size());
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_inv, bi.size());
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_fwd, bf.data(), bf.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_inv, bi.data(), bi.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, sizeof(lt::PgaScalars));
+  if (e != cudaSuccess) { lt_ctx_destroy(reinterpret_cast<lt_ctx>(c)); return LT_ERR_CUDA; }
+  *out = reinterpret_cast<lt_ctx>(c);
+  return LT_OK;
+}
+
+lt_status lt_ctx_destroy(lt_ctx ctx) {
+  if (!ctx) return LT_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  cudaDeviceSynchronize();  // pending work may still read the context's buffers
+  if (c->d_fwd) cudaFree(c->d_fwd);
+  if (c->d_inv) cudaFree(c->d_inv);
+  if (c->d_status) cudaFree(c->d_status);
+  if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  delete c;
+  return LT_OK;
+}
+
+lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
+  if (!ctx) return LT_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  switch (opt) {
+    case LT_OPT_MAX_SWEEPS:
+      if (!(value >= 1 && value <= 1000)) return LT_ERR_ARG;
+      c->max_sweeps = (int)value;
+      return LT_OK;
+    case LT_OPT_JACOBI_TOL:
+      if (!(value < 1.0)) return LT_ERR_ARG;
+      c->jacobi_tol = value > 0 ? value : 0.0;
+      return LT_OK;
+    case LT_OPT_OBJECTIVE:
+      c->objective = value != 0.0;
+      return LT_OK;
+  }
+  return LT_ERR_ARG;
+}
+
+lt_status lt_workspace_size(lt_ctx ctx, lt_op op, int64_t I1, int64_t I2, int64_t I2b,
+                            size_t* out) {
+  if (!ctx || !out) return LT_ERR_ARG;
+  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  lt_status s = check_dims(I1, I2);
+  if (s != LT_OK) return s;
+  *out = 0;
+  switch (op) {
+    case LT_OP_TRANSFORM:
+    case LT_OP_INVERSE: {
+      lt::TransformPlan p;
+      return lt::plan_transform(c, I1 * I2, op == LT_OP_INVERSE, &p);
+    }
+    case LT_OP_PRODUCT: {
+      s = check_dims(I2, I2b);
+      if (s != LT_OK) return s;
+      *out = align256((size_t)I1 * I2 * c.P * c.elem) + align256((size_t)I2 * I2b * c.P * c.elem);
+      return LT_OK;
+    }
+    case LT_OP_SVD: {
+      lt::JacobiPlan jp;
+      s = lt::plan_jacobi(c, lt::JAC_SVD, I1, I2, &jp);
+      if (s != LT_OK) return s;
+      *out = align256((size_t)I1 * I2 * c.P * c.elem) + align256(jp.ws_bytes);
+      return LT_OK;
+    }
+    case LT_OP_SVT: {
+      lt::JacobiPlan jp;
+      s = lt::plan_jacobi(c, lt::JAC_SVT, I1, I2, &jp);
+      if (s != LT_OK) return s;
+      *out = align256(jp.ws_bytes);
+      return LT_OK;
+    }
+    case LT_OP_PGA: {
+      PgaLayout L;
+      s = pga_layout(c, I1, I2, &L);
+      if (s != LT_OK) return s;
+      *out = L.total;
+      return LT_OK;
+    }
+  }
+  return LT_ERR_ARG;
+}
+
+lt_status lt_transform(lt_ctx ctx, int64_t I1, int64_t I2, const void* X, void* X_hat,
+                       void* ws, size_t ws_bytes, void* stream) {
+  (void)ws; (void)ws_bytes;
+  if (check_ctx(ctx) != LT_OK || !X || !X_hat) return LT_ERR_ARG;
+  lt_status s = check_dims(I1, I2);
+  if (s != LT_OK) return s;
+  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  lt::TransformPlan plan;
+  s = lt::plan_transform(c, I1 * I2, false, &plan);
+  if (s != LT_OK) return s;
+  return cuda_status(lt::launch_transform(c, plan, X, X_hat, lt::FUSE_NONE, nullptr,
+                                          (cudaStream_t)stream, nullptr));
+}
+
+lt_status lt_inverse(lt_ctx ctx, int64_t I1, int64_t I2, const void* X_hat, void* X,
+                     void* ws, size_t ws_bytes, void* stream) {
+  (void)ws; (void)ws_bytes;
+  if (check_ctx(ctx) != LT_OK || !X || !X_hat) return LT_ERR_ARG;
+  lt_status s = check_dims(I1, I2);
+  if (s != LT_OK) return s;
+  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  lt::TransformPlan plan;
+  s = lt::plan_transform(c, I1 * I2, true, &plan);
+  if (s != LT_OK) return s;
+  return cuda_status(lt::launch_transform(c, plan, X_hat, X, lt::FUSE_NONE, nullptr,
+                                          (cudaStream_t)stream, nullptr));
+}
+
+lt_status lt_product(lt_ctx ctx, int64_t I1, int64_t l, int64_t I2, const void* A,
+                     const void* B, void* C, void* ws, size_t ws_bytes, void* stream) {
+  if (check_ctx(ctx) != LT_OK || !A || !B || !C) return LT_ERR_ARG;
+  if (C == A || C == B) return LT_ERR_ARG;
+  lt_status s = check_dims(I1, l);
+  if (s == LT_OK) s = check_dims(l, I2);
+  if (s != LT_OK) return s;
+  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  size_t need = 0;
+  s = lt_workspace_size(ctx, LT_OP_PRODUCT, I1, l, I2, &need);
+  if (s != LT_OK) return s;
+  s = check_ws(ws, ws_bytes, need);
+  if (s != LT_OK) return s;
+  lt::TransformPlan pa, pb, pc;
+  if ((s = lt::plan_transform(c, I1 * l, false, &pa)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, l * I2, false, &pb)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, I1 * I2, true, &pc)) != LT_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  void* Ah = w;
+  void* Bh = w + align256((size_t)I1 * l * c.P * c.elem);
+  cudaError_t e = lt::launch_transform(c, pa, A, Ah, lt::FUSE_NONE, nullptr, st, nullptr);
+  if (e == cudaSuccess) e = lt::launch_transform(c, pb, B, Bh, lt::FUSE_NONE, nullptr, st, nullptr);
+  if (e == cudaSuccess) e = lt::launch_facewise_gemm(c, I1, I2, l, Ah, Bh, C, st);
+  if (e == cudaSuccess) e = lt::launch_transform(c, pc, C, C, lt::FUSE_NONE, nullptr, st, nullptr);
+  return cuda_status(e);
+}
+
+lt_status lt_svd(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, void* U, void* S,
+                 void* V, void* sigma, void* ws, size_t ws_bytes, void* stream) {
+  if (check_ctx(ctx) != LT_OK || !A || !U || !S || !V) return LT_ERR_ARG;
+  lt_status s = check_dims(I1, I2);
+  if (s != LT_OK) return s;
+  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  size_t need = 0;
+  if ((s = lt_workspace_size(ctx, LT_OP_SVD, I1, I2, 0, &need)) != LT_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, need)) != LT_OK) return s;
+  lt::JacobiPlan jp;
+  lt::TransformPlan pa, pu, ps, pv;
+  if ((s = lt::plan_jacobi(c, lt::JAC_SVD, I1, I2, &jp)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, I1 * I2, false, &pa)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, I1 * I1, true, &pu)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, I1 * I2, true, &ps)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, I2 * I2, true, &pv)) != LT_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  void* Ah = w;
+  lt::JacobiIO io;
+  io.A = Ah;
+  io.U = U;
+  io.S = S;
+  io.V = V;
+  io.sigma = sigma;
+  io.scratch = w + align256((size_t)I1 * I2 * c.P * c.elem);
+  cudaError_t e = lt::launch_transform(c, pa, A, Ah, lt::FUSE_NONE, nullptr, st, nullptr);
+  if (e == cudaSuccess) e = lt::launch_jacobi(c, jp, io, st);
+  if (e == cudaSuccess) e = lt::launch_transform(c, pu, U, U, lt::FUSE_NONE, nullptr, st, nullptr);
+  if (e == cudaSuccess) e = lt::launch_transform(c, ps, S, S, lt::FUSE_NONE, nullptr, st, nullptr);
+  if (e == cudaSuccess) e = lt::launch_transform(c, pv, V, V, lt::FUSE_NONE, nullptr, st, nullptr);
+  return cuda_status(e);
+}
+
+lt_status lt_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau, void* D,
+                 void* ws, size_t ws_bytes, void* stream) {
+  if (check_ctx(ctx) != LT_OK || !A || !D) return LT_ERR_ARG;
+  if (!(tau >= 0.0) || !std::isfinite(tau)) return LT_ERR_ARG;
+  lt_status s = check_dims(I1, I2);
+  if (s != LT_OK) return s;
+  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  size_t need = 0;
+  if ((s = lt_workspace_size(ctx, LT_OP_SVT, I1, I2, 0, &need)) != LT_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, need)) != LT_OK) return s;
+  lt::JacobiPlan jp;
+  lt::TransformPlan pf, pi;
+  if ((s = lt::plan_jacobi(c, lt::JAC_SVT, I1, I2, &jp)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, I1 * I2, false, &pf)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, I1 * I2, true, &pi)) != LT_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  lt::JacobiIO io;
+  io.A = D;
+  io.D = D;
+  io.tau = tau;
+  io.scratch = ws;
+  cudaError_t e = lt::launch_transform(c, pf, A, D, lt::FUSE_NONE, nullptr, st, nullptr);
+  if (e == cudaSuccess) e = lt::launch_jacobi(c, jp, io, st);
+  if (e == cudaSuccess) e = lt::launch_transform(c, pi, D, D, lt::FUSE_NONE, nullptr, st, nullptr);
+  return cuda_status(e);
+}
+
+lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8_t* mask,
+                          const void* obs, double tau, double step, int64_t iters,
+                          double tol, void* X, lt_pga_state* state, lt_pga_report* report,
+                          void* ws, size_t ws_bytes, void* stream) {
+  if (check_ctx(ctx) != LT_OK || !mask || !obs || !X) return LT_ERR_ARG;
+  if (!(tau >= 0.0) || !std::isfinite(tau) || !(step > 0.0) || !std::isfinite(step)) return LT_ERR_ARG;
+  if (iters < 0 || !(tol >= 0.0)) return LT_ERR_ARG;
+  if (state && (state->X_prev == nullptr || state->X_prev == X || state->k < 0)) return LT_ERR_ARG;
+  lt_status s = check_dims(I1, I2);
+  if (s != LT_OK) return s;
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  PgaLayout L;
+  if ((s = pga_layout(c, I1, I2, &L)) != LT_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, L.total)) != LT_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  const size_t bytes = (size_t)I1 * I2 * c.P * c.elem;
+  void* X2 = w + L.x2;
+  void* Gh = w + L.ghat;
+  double* partials = reinterpret_cast<double*>(w + L.partials);
+  lt::PgaScalars* scal = reinterpret_cast<lt::PgaScalars*>(w + L.scal);
+  lt::SliceInfo* info = reinterpret_cast<lt::SliceInfo*>(w + L.info);
+
+  const bool resume = state && state->k > 0;
+  cudaError_t e = lt::launch_copy_bytes(X2, resume ? state->X_prev : X, bytes, st);
+  if (e == cudaSuccess)
+    e = lt::launch_pga_init(scal, resume ? state->t_prev : 1.0, resume ? state->t : 1.0,
+                            resume ? state->k : 0, tol, st);
+  lt::PgaFuse f;
+  f.mask = mask;
+  f.obs = obs;
+  f.step = step;
+  f.scal = scal;
+  f.partials = partials;
+  f.objective = c.objective;
+  lt::JacobiIO io;
+  io.A = Gh;
+  io.D = Gh;
+  io.tau = step * tau;
+  io.scal = scal;
+  io.scratch = w + L.jac;
+  io.info = info;
+  for (int64_t j = 0; j < iters && e == cudaSuccess; ++j) {
+    void* cur = (j % 2 == 0) ? X : X2;
+    void* old = (j % 2 == 0) ? X2 : X;
+    f.x_cur = cur;
+    f.x_old = old;
+    f.x_out = old;
+    int rows = 0;
+    e = lt::launch_transform(c, L.fwd, nullptr, Gh, lt::FUSE_PGA_FORWARD, &f, st, nullptr);
+    if (e == cudaSuccess) e = lt::launch_jacobi(c, L.jp, io, st);
+    if (e == cudaSuccess)
+      e = lt::launch_transform(c, L.inv, Gh, Gh, lt::FUSE_PGA_INVERSE, &f, st, &rows);
+    if (e == cudaSuccess)
+      e = lt::launch_pga_finish(scal, partials, rows, info, c.P, tau, c.objective,
+                                c.d_status, st);
+  }
+  if (e == cudaSuccess)
+    e = lt::launch_select_result(scal, X, X2, state ? state->X_prev : nullptr, bytes, st);
+  if (e == cudaSuccess && (report || state)) {
+    e = cudaMemcpyAsync(c.h_pinned, scal, sizeof(lt::PgaScalars), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) {
+      ReportJob* job = new ReportJob{static_cast<const lt::PgaScalars*>(c.h_pinned), report, state};
+      e = cudaLaunchHostFunc(st, report_cb, job);
+      if (e != cudaSuccess) delete job;
+    }
+  }
+  return cuda_status(e);
+}
+
+lt_status lt_workspace_size_batched(int nprob, const lt_ctx* ctxs, const int64_t* I1,
+                                    const int64_t* I2, size_t* out) {
+  if (nprob < 1 || !ctxs || !I1 || !I2 || !out) return LT_ERR_ARG;
+  size_t total = 0;
+  for (int i = 0; i < nprob; ++i) {
+    size_t b = 0;
+    lt_status s = lt_workspace_size(ctxs[i], LT_OP_PGA, I1[i], I2[i], 0, &b);
+    if (s != LT_OK) return s;
+    total += align256(b);
+  }
+  *out = total;
+  return LT_OK;
+}
+
+lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const int64_t* I1,
+                                  const int64_t* I2, const uint8_t* const* mask,
+                                  const void* const* obs, const double* tau,
+                                  const double* step, int64_t iters, void* const* X,
+                                  lt_pga_report* reports, void* ws, size_t ws_bytes,
+                                  void* stream) {
+  if (nprob < 1 || !ctxs || !I1 || !I2 || !mask || !obs || !tau || !step || !X) return LT_ERR_ARG;
+  size_t need = 0;
+  lt_status s = lt_workspace_size_batched(nprob, ctxs, I1, I2, &need);
+  if (s != LT_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, need)) != LT_OK) return s;
+  const lt_precision prec = reinterpret_cast<Ctx*>(ctxs[0])->prec;
+  for (int i = 0; i < nprob; ++i)
+    if (reinterpret_cast<Ctx*>(ctxs[i])->prec != prec) return LT_ERR_ARG;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  size_t off = 0;
+  for (int i = 0; i < nprob; ++i) {
+    size_t b = 0;
+    lt_workspace_size(ctxs[i], LT_OP_PGA, I1[i], I2[i], 0, &b);
+    s = lt_pga_complete(ctxs[i], I1[i], I2[i], mask[i], obs[i], tau[i], step[i], iters, 0.0,
+                        X[i], nullptr, reports ? &reports[i] : nullptr, w + off, b, stream);
+    if (s != LT_OK) return s;
+    off += align256(b);
+  }
+  return LT_OK;
+}
+
+lt_status lt_last_device_status(lt_ctx ctx, int32_t* out) {
+  if (!ctx || !out) return LT_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  cudaError_t e = cudaDeviceSynchronize();
+  int32_t v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  *out = v;
+  return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Kernel G: the generalized face-wise product of Sec. 3.1, C^p = A^p B^p for every
+// frontal slice p (the loop of Algorithm 2), all slices in one launch
+// (blockIdx.z = p).  Column-major slices: A^p is M x Kd, B^p is Kd x N, C^p is M x N.
+//
+// SIMT path (LT_FP64, LT_FP32): 64 x 64 output tile per CTA, 16-deep K steps staged in
+// shared memory, 4 x 4 register tile per thread.
+#include "lt_internal.cuh"
+
+namespace lt {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+constexpr int kGThreads = (BM / TM) * (BN / TN);  // 256
+
+template <typename T>
+__global__ void __launch_bounds__(kGThreads)
+facewise_gemm_simt(int64_t M, int64_t N, int64_t Kd, int64_t P, const T* __restrict__ A,
+                   const T* __restrict__ B, T* __restrict__ C) {
+  __shared__ T As[BK][BM];
+  __shared__ T Bs[BK][BN + 1];
+  for (int64_t p = blockIdx.z; p < P; p += gridDim.z) {
+  const T* Ap = A + p * M * Kd;
+  const T* Bp = B + p * Kd * N;
+  T* Cp = C + p * M * N;
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int tx = threadIdx.x % (BN / TN), ty = threadIdx.x / (BN / TN);
+  T acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = T(0);
+
+  for (int64_t k0 = 0; k0 < Kd; k0 += BK) {
+    for (int idx = threadIdx.x; idx < BM * BK; idx += kGThreads) {
+      const int mm = idx % BM, kk = idx / BM;
+      const int64_t gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < Kd) ? Ap[gm + M * gk] : T(0);
+    }
+    for (int idx = threadIdx.x; idx < BK * BN; idx += kGThreads) {
+      const int kk = idx % BK, nn = idx / BK;
+      const int64_t gk = k0 + kk, gn = n0 + nn;
+      Bs[kk][nn] = (gk < Kd && gn < N) ? Bp[gk + Kd * gn] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int64_t gm = m0 + ty * TM + i, gn = n0 + tx * TN + j;
+      if (gm < M && gn < N) Cp[gm + M * gn] = acc[i][j];
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_facewise_gemm(const Ctx& c, int64_t M, int64_t N, int64_t Kd,
+                                 const void* A, const void* B, void* C, cudaStream_t st) {
+  const int64_t gz = c.P < 65535 ? c.P : 65535;
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)gz);
+  if (c.elem == 8)
+    facewise_gemm_simt<double><<<grid, kGThreads, 0, st>>>(
+        M, N, Kd, c.P, (const double*)A, (const double*)B, (double*)C);
+  else
+    facewise_gemm_simt<float><<<grid, kGThreads, 0, st>>>(
+        M, N, Kd, c.P, (const float*)A, (const float*)B, (float*)C);
+  return cudaGetLastError();
+}
+
+}  // namespace lt

@@ -1,0 +1,160 @@
+// Internal declarations shared by the liblt translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lt.h"
+
+namespace lt {
+
+constexpr int kMaxModes = 8;          // K <= 10
+constexpr int kSmemOptin = 232448;    // opt-in shared memory per block on sm_103
+constexpr int kNumSMs = 152;          // grid sizing default; refined at context creation
+
+// ----------------------------------------------------------------------------------
+// Context
+// ----------------------------------------------------------------------------------
+struct Ctx {
+  int K = 0;
+  int nmodes = 0;                     // K - 2
+  int64_t sizes[kMaxModes] = {};      // I3..IK
+  int64_t P = 0;
+  lt_precision prec = LT_FP64;
+  int elem = 8;                       // bytes per element
+  int sms = kNumSMs;
+  int device = 0;
+  // Device copies (context precision), row-major I x I each, mode order 3..K.
+  void* d_fwd = nullptr;
+  void* d_inv = nullptr;
+  int64_t mat_off[kMaxModes] = {};    // element offset of mode k's matrix
+  int32_t* d_status = nullptr;        // device status word (LT_DEV_* bits)
+  // Options
+  int max_sweeps = 40;
+  double jacobi_tol = 0.0;            // <= 0: default
+  int objective = 0;
+  // Pinned host staging for asynchronous reports
+  void* h_pinned = nullptr;
+};
+
+// ----------------------------------------------------------------------------------
+// Transform (kernel T): a pass applies a contiguous group of modes to a view
+// [outer][Pg][Sg] of the tensor, tiled over Sg.  Element (o, p, s) sits at
+// o*Pg*Sg + p*Sg + s.
+// ----------------------------------------------------------------------------------
+enum FuseMode { FUSE_NONE = 0, FUSE_PGA_FORWARD = 1, FUSE_PGA_INVERSE = 2 };
+
+struct PgaScalars {        // lives in the workspace, device side
+  double t_prev;           // t_{k-1}
+  double t;                // t_k
+  double beta;             // (t_{k-1} - 1) / t_k for the next iteration
+  double rel_residual;     // of the last iteration
+  double objective;        // of the last iteration (if enabled)
+  double tol;
+  int64_t k_done;          // iterations completed in this call
+  int64_t k_total;         // global iteration counter (resume)
+  int32_t done;            // tolerance reached: remaining launches return at once
+  int32_t max_sweeps_used;
+  int32_t status;          // LT_DEV_* bits of this call
+  int32_t pad;
+};
+
+struct PgaFuse {
+  const void* x_cur = nullptr;      // X^k
+  const void* x_old = nullptr;      // X^{k-1}
+  void* x_out = nullptr;            // X^{k+1} (may equal x_old)
+  const uint8_t* mask = nullptr;
+  const void* obs = nullptr;
+  double step = 1.0;
+  const PgaScalars* scal = nullptr;
+  double* partials = nullptr;       // [grid][4]: sum (y-x)^2, sum x^2, sum mask(x-obs)^2
+  int objective = 0;
+};
+
+struct TransformPass {
+  int nm = 0;                         // modes in this pass (application order)
+  int msize[kMaxModes] = {};
+  int mstride[kMaxModes] = {};        // stride of the mode inside Pg
+  int64_t mat_off[kMaxModes] = {};    // element offsets of the matrices to apply
+  int64_t Pg = 1, Sg = 1, outer = 1;
+  int ts = 32;                        // tile width along Sg
+  int smem = 0;                       // bytes
+};
+
+struct TransformPlan {
+  bool inverse = false;               // matrices from d_inv instead of d_fwd
+  int npass = 0;
+  TransformPass pass[kMaxModes];
+};
+
+// Build the pass plan for slices of S elements, forward (inverse = false) or inverse.
+lt_status plan_transform(const Ctx& c, int64_t S, bool inverse, TransformPlan* plan);
+
+// Enqueue the passes.  `fuse` (nullable) applies the PGA prologue on the first pass
+// or the epilogue on the last pass.  `grid_out` returns the grid of the last pass
+// (number of partial-sum rows written when fusing the epilogue).
+cudaError_t launch_transform(const Ctx& c, const TransformPlan& plan, const void* in,
+                             void* out, int fuse_mode, const PgaFuse* fuse,
+                             cudaStream_t st, int* grid_out);
+int transform_grid(const Ctx& c, const TransformPass& p);
+
+// ----------------------------------------------------------------------------------
+// Face-wise GEMM (kernel G): C^p = A^p B^p, column-major per slice.
+// ----------------------------------------------------------------------------------
+cudaError_t launch_facewise_gemm(const Ctx& c, int64_t M, int64_t N, int64_t Kd,
+                                 const void* A, const void* B, void* C, cudaStream_t st);
+
+// ----------------------------------------------------------------------------------
+// Jacobi SVD / SVT (kernel J), one CTA per slice.
+// ----------------------------------------------------------------------------------
+enum JacobiMode { JAC_SVT = 0, JAC_SVD = 1 };
+
+struct JacobiPlan {
+  int mode = JAC_SVT;
+  int64_t I1 = 0, I2 = 0, P = 0;
+  int m = 0, n = 0, npad = 0, ld = 0;  // working matrix m x n (m >= n), leading dim
+  bool transposed = false;              // working matrix is A^T (I1 < I2)
+  bool w_in_smem = true;
+  int E = 1;                            // elements per lane per column chunk
+  int threads = 512;
+  int smem = 0;
+  size_t ws_bytes = 0;                  // scratch bytes (global W, Jacobi V, info)
+};
+
+struct SliceInfo {          // per slice, written by the Jacobi kernel
+  int32_t sweeps;
+  int32_t rank;             // singular values above the threshold
+  double nuclear;           // sum of the shrunk singular values
+};
+
+lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan* jp);
+
+struct JacobiIO {
+  const void* A = nullptr;  // input slices (transform domain)
+  void* D = nullptr;        // SVT output (may alias A)
+  void* U = nullptr;        // SVD outputs (transform domain)
+  void* S = nullptr;
+  void* V = nullptr;
+  void* sigma = nullptr;    // optional, min(I1,I2) per slice
+  double tau = 0.0;         // SVT threshold (host value)
+  const PgaScalars* scal = nullptr;  // PGA: skip when done
+  void* scratch = nullptr;  // jp.ws_bytes
+  SliceInfo* info = nullptr;
+};
+
+cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io,
+                          cudaStream_t st);
+
+// ----------------------------------------------------------------------------------
+// PGA bookkeeping kernels
+// ----------------------------------------------------------------------------------
+cudaError_t launch_pga_init(PgaScalars* scal, double t_prev, double t, int64_t k0,
+                            double tol, cudaStream_t st);
+cudaError_t launch_pga_finish(PgaScalars* scal, const double* partials, int rows,
+                              const SliceInfo* info, int64_t P, double tau, int objective,
+                              int32_t* ctx_status, cudaStream_t st);
+cudaError_t launch_copy_bytes(void* dst, const void* src, size_t bytes, cudaStream_t st);
+cudaError_t launch_select_result(const PgaScalars* scal, void* x_user, const void* x_alt,
+                                 void* x_prev_out, size_t bytes, cudaStream_t st);
+
+}  // namespace lt

@@ -1,0 +1,514 @@
+// Kernel J: per-slice SVD in the transform domain (Algorithm 3, line "svd(A_hat^i)")
+// and the singular value thresholding of Algorithm 4 (shrink max(sigma - tau, 0) and
+// reconstruct U S V^T), one CTA per frontal slice.
+//
+// Method: one-sided (Hestenes) Jacobi on the working matrix B (m x n, m >= n): B = A^p
+// when I1 >= I2, B = (A^p)^T otherwise, so that the n <= m columns are orthogonalised.
+// Plane rotations are applied from the right, B <- B J, until every pair of columns is
+// orthogonal to the tolerance: |b_i . b_j| <= tol * ||b_i|| ||b_j||.  At convergence
+// B = W = U Sigma (columns of norm sigma_i) and the accumulated rotations are V.
+// Rotation parameters follow Rutishauser's formulas (Golub & Van Loan, Matrix
+// Computations, 4th ed., Sec. 8.6.3): zeta = (beta - alpha)/(2 gamma),
+// t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t, with
+// alpha = ||b_i||^2, beta = ||b_j||^2, gamma = b_i . b_j; the squared norms are updated
+// as alpha - t gamma, beta + t gamma and recomputed exactly at the start of each sweep.
+//
+// Parallel ordering: round-robin ("circle") tournament over the n (padded to even)
+// columns: n - 1 rounds of n/2 disjoint pairs per sweep; a warp owns one pair at a time
+// and keeps both columns in registers (lane l holds rows l, l+32, ...), so a pair costs
+// one read and one write of its two columns plus a warp-shuffle reduction of b_i . b_j.
+//
+// SVT reconstruction without V: with W = B V (orthogonal columns w_i, ||w_i|| = sigma_i)
+// the shrunk slice is D_B = W diag((sigma - tau)_+ / sigma) V^T, and since
+// V^T = Sigma^{-2} W^T B, D_B = sum_{sigma_i > tau} g_i w_i (w_i^T B) with
+// g_i = (sigma_i - tau) / sigma_i^3: every column b_j of the ORIGINAL slice is mapped
+// to D_B b_j by k dot products and k axpys (k = number of sigma_i > tau).  V is never
+// formed, so the rotations only touch B.
+#include <algorithm>
+#include <cfloat>
+
+#include "lt_internal.cuh"
+
+namespace lt {
+namespace {
+
+constexpr int kJThreads = 512;
+constexpr int kWarps = kJThreads / 32;
+
+template <typename T>
+__device__ __forceinline__ T warp_allsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T> __device__ __forceinline__ T unit_roundoff();
+template <> __device__ __forceinline__ double unit_roundoff<double>() { return DBL_EPSILON / 2; }
+template <> __device__ __forceinline__ float unit_roundoff<float>() { return FLT_EPSILON / 2; }
+
+// Round-robin pairing: column n-1 is fixed, the others rotate on a circle.
+__device__ __forceinline__ void rr_pair(int r, int k, int n, int& i, int& j) {
+  const int c = n - 1;
+  if (k == 0) {
+    i = c;
+    j = r;
+  } else {
+    i = (r + k) % c;
+    j = (r - k + c) % c;
+  }
+}
+
+// Rotation for the pair (alpha, beta, gamma).  The angle only steers convergence; what
+// must hold to working precision is c^2 + s^2 = 1, so that B J stays an orthogonal
+// transform of B.  FP32: Rutishauser's formulas directly.  FP64: the tangent t is
+// taken from the same formulas in FP32 (FP64 divides and square roots cost tens of
+// FP64 pipe slots each on this GPU), then c = (1 + t^2)^{-1/2} is computed in FP64 by
+// two Newton steps y <- y (3 - x y^2) / 2 from the FP32 reciprocal square root
+// (2^-22 -> 2^-44 -> full precision), s = c t.  A tangent that is only FP32-accurate
+// leaves |b_i . b_j| at ~1e-7 of its value after the rotation; later sweeps remove it.
+__device__ __forceinline__ void rotation(float al, float be, float g, float& cs, float& sn,
+                                         float& t) {
+  const float zeta = (be - al) / (2.f * g);
+  const float az = fabsf(zeta);
+  t = (az > 1e15f) ? 0.5f / az : 1.f / (az + sqrtf(1.f + az * az));
+  if (zeta < 0.f) t = -t;
+  cs = rsqrtf(1.f + t * t);
+  sn = cs * t;
+}
+__device__ __forceinline__ void rotation(double al, double be, double g, double& cs,
+                                         double& sn, double& t) {
+  const float zeta = float(be - al) / (2.f * float(g));
+  const float az = fabsf(zeta);
+  float tf = (az > 1e15f) ? 0.5f / az : 1.f / (az + sqrtf(1.f + az * az));
+  if (zeta < 0.f) tf = -tf;
+  t = double(tf);
+  const double x = fma(t, t, 1.0);
+  double y = double(rsqrtf(float(x)));
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  cs = y;
+  sn = y * t;
+}
+
+struct JArgs {
+  JacobiPlan jp;
+  JacobiIO io;
+  double tol;
+  int max_sweeps;
+  int32_t* status;
+};
+
+template <typename T, int E>
+__global__ void __launch_bounds__(kJThreads)
+jacobi_kernel(const JArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const JacobiPlan& jp = a.jp;
+  if (a.io.scal != nullptr && a.io.scal->done) return;  // PGA converged earlier
+
+  const int m = jp.m, n = jp.n, np = jp.npad, ld = jp.ld;
+  const int64_t I1 = jp.I1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T tol2 = T(a.tol) * T(a.tol);
+
+  // shared memory carve-up
+  unsigned char* sp = smem_raw;
+  T* Ws = nullptr;
+  if (jp.w_in_smem) { Ws = reinterpret_cast<T*>(sp); sp += sizeof(T) * (size_t)ld * np; }
+  T* nrm = reinterpret_cast<T*>(sp); sp += sizeof(T) * np;
+  int* list = reinterpret_cast<int*>(sp); sp += sizeof(int) * np;        // SVT: kept columns / SVD: rank
+  T* coef = reinterpret_cast<T*>(sp); sp += sizeof(T) * (size_t)kWarps * np;  // per-warp coefficients
+  T* vtmp = reinterpret_cast<T*>(sp); sp += sizeof(T) * (size_t)(jp.mode == JAC_SVD ? 2 * m : 0);
+  __shared__ int s_count, s_cand;
+  __shared__ T s_red[kWarps];
+
+  const T* Ain = reinterpret_cast<const T*>(a.io.A);
+  unsigned char* scratch = reinterpret_cast<unsigned char*>(a.io.scratch);
+  T* Wg = jp.w_in_smem ? nullptr
+                       : reinterpret_cast<T*>(scratch) + (size_t)blockIdx.x * ld * np;
+  // Jacobi V (SVD mode only): np x np per CTA, after the global W regions
+  T* Vj = nullptr;
+  if (jp.mode == JAC_SVD) {
+    size_t off = jp.w_in_smem ? 0 : (size_t)gridDim.x * ld * np;
+    Vj = reinterpret_cast<T*>(scratch) + off + (size_t)blockIdx.x * np * np;
+  }
+  T* W = jp.w_in_smem ? Ws : Wg;
+
+  for (int64_t slice = blockIdx.x; slice < jp.P; slice += gridDim.x) {
+    const T* A = Ain + slice * jp.I1 * jp.I2;
+    // ---- load B (transposed when I1 < I2); zero padding column(s)
+    if (!jp.transposed) {
+      for (int idx = threadIdx.x; idx < m * np; idx += blockDim.x) {
+        const int r = idx % m, c = idx / m;
+        W[r + (size_t)ld * c] = (c < n) ? A[r + I1 * c] : T(0);
+      }
+    } else {
+      for (int idx = threadIdx.x; idx < n * m; idx += blockDim.x) {
+        const int c = idx % n, r = idx / n;
+        W[r + (size_t)ld * c] = A[c + I1 * r];
+      }
+      for (int idx = threadIdx.x; idx < m * (np - n); idx += blockDim.x)
+        W[idx % m + (size_t)ld * (n + idx / m)] = T(0);
+    }
+    if (jp.mode == JAC_SVD) {
+      for (int idx = threadIdx.x; idx < np * np; idx += blockDim.x)
+        Vj[idx] = (idx % np == idx / np) ? T(1) : T(0);
+    }
+    __syncthreads();
+
+    // ---- sweeps
+    int sweeps = 0;
+    bool rotated = true;
+    while (rotated && sweeps < a.max_sweeps) {
+      for (int c = warp; c < np; c += kWarps) {
+        const T* col = W + (size_t)ld * c;
+        T acc = T(0);
+        for (int r = lane; r < m; r += 32) acc = fma(col[r], col[r], acc);
+        acc = warp_allsum(acc);
+        if (lane == 0) nrm[c] = acc;
+      }
+      __syncthreads();
+      int flag = 0;
+      for (int rnd = 0; rnd < np - 1; ++rnd) {
+        for (int k = warp; k < np / 2; k += kWarps) {
+          int i, j;
+          rr_pair(rnd, k, np, i, j);
+          T* ci = W + (size_t)ld * i;
+          T* cj = W + (size_t)ld * j;
+          T x[E], y[E];
+          T g = T(0);
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int r = lane + 32 * e;
+            x[e] = (r < m) ? ci[r] : T(0);
+            y[e] = (r < m) ? cj[r] : T(0);
+            g = fma(x[e], y[e], g);
+          }
+          g = warp_allsum(g);
+          const T al = nrm[i], be = nrm[j];
+          if (al > T(0) && be > T(0) && g * g > tol2 * al * be) {
+            T cs, sn, t;
+            rotation(al, be, g, cs, sn, t);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              const int r = lane + 32 * e;
+              const T xi = x[e], yi = y[e];
+              if (r < m) {
+                ci[r] = cs * xi - sn * yi;
+                cj[r] = sn * xi + cs * yi;
+              }
+            }
+            if (jp.mode == JAC_SVD) {
+              T* vi = Vj + (size_t)np * i;
+              T* vj = Vj + (size_t)np * j;
+              for (int r = lane; r < np; r += 32) {
+                const T xi = vi[r], yi = vj[r];
+                vi[r] = cs * xi - sn * yi;
+                vj[r] = sn * xi + cs * yi;
+              }
+            }
+            if (lane == 0) {
+              nrm[i] = al - t * g;
+              nrm[j] = be + t * g;
+            }
+            flag = 1;
+          }
+        }
+        __syncthreads();
+      }
+      rotated = __syncthreads_or(flag) != 0;
+      ++sweeps;
+    }
+    // exact final norms
+    for (int c = warp; c < np; c += kWarps) {
+      const T* col = W + (size_t)ld * c;
+      T acc = T(0);
+      for (int r = lane; r < m; r += 32) acc = fma(col[r], col[r], acc);
+      acc = warp_allsum(acc);
+      if (lane == 0) nrm[c] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int st = 0;
+      if (rotated) st |= LT_DEV_NOCONV;
+      for (int c = 0; c < n; ++c)
+        if (!isfinite(nrm[c])) { st |= LT_DEV_NONFINITE; break; }
+      if (st) atomicOr(a.status, st);
+      if (a.io.info) a.io.info[slice].sweeps = sweeps;
+    }
+
+    if (jp.mode == JAC_SVT) {
+      // ---- shrink: keep columns with sigma > tau, g_i = (sigma_i - tau)/sigma_i^3
+      const T tau = T(a.io.tau);
+      if (threadIdx.x == 0) {
+        int k = 0;
+        T nuc = T(0);
+        for (int c = 0; c < n; ++c) {
+          const T sg = sqrt(nrm[c]);
+          if (sg > tau) {
+            list[k++] = c;
+            nuc += sg - tau;
+          }
+        }
+        s_count = k;
+        if (a.io.info) {
+          a.io.info[slice].rank = k;
+          a.io.info[slice].nuclear = double(nuc);
+        }
+      }
+      __syncthreads();
+      const int k = s_count;
+      T* gcoef = nrm;  // reuse: nrm[c] -> g_c for kept columns
+      for (int q = threadIdx.x; q < k; q += blockDim.x) {
+        const int c = list[q];
+        const T sg = sqrt(nrm[c]);
+        gcoef[c] = ((sg - tau) / sg) / sg / sg;
+      }
+      __syncthreads();
+      // ---- reconstruct D_B = sum_i g_i w_i (w_i^T b_j), column by column
+      T* D = reinterpret_cast<T*>(a.io.D) + slice * jp.I1 * jp.I2;
+      T* cw = coef + (size_t)warp * np;
+      for (int j = warp; j < n; j += kWarps) {
+        T b[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int r = lane + 32 * e;
+          b[e] = (r < m) ? (jp.transposed ? A[j + I1 * r] : A[r + I1 * j]) : T(0);
+        }
+        for (int q = 0; q < k; ++q) {
+          const T* w = W + (size_t)ld * list[q];
+          T d = T(0);
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int r = lane + 32 * e;
+            if (r < m) d = fma(w[r], b[e], d);
+          }
+          d = warp_allsum(d);
+          if (lane == 0) cw[q] = d * gcoef[list[q]];
+        }
+        __syncwarp();
+        T out[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) out[e] = T(0);
+        for (int q = 0; q < k; ++q) {
+          const T cq = cw[q];
+          const T* w = W + (size_t)ld * list[q];
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int r = lane + 32 * e;
+            if (r < m) out[e] = fma(cq, w[r], out[e]);
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int r = lane + 32 * e;
+          if (r < m) {
+            if (jp.transposed) D[j + I1 * r] = out[e];
+            else D[r + I1 * j] = out[e];
+          }
+        }
+        __syncwarp();
+      }
+    } else {
+      // ---- SVD: sort descending, write Sigma, the Jacobi V side and the W side
+      const int64_t I2 = jp.I2;
+      T sig_max = T(0);
+      for (int c = 0; c < n; ++c) sig_max = fmax(sig_max, sqrt(nrm[c]));
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const T sc = nrm[c];
+        int rk = 0;
+        for (int c2 = 0; c2 < n; ++c2) {
+          const T s2 = nrm[c2];
+          rk += (s2 > sc) || (s2 == sc && c2 < c);
+        }
+        list[c] = rk;
+      }
+      __syncthreads();
+      T* S = reinterpret_cast<T*>(a.io.S) + slice * I1 * I2;
+      for (int64_t idx = threadIdx.x; idx < I1 * I2; idx += blockDim.x) S[idx] = T(0);
+      __syncthreads();
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const T sg = sqrt(nrm[c]);
+        S[list[c] + I1 * list[c]] = sg;
+        if (a.io.sigma) reinterpret_cast<T*>(a.io.sigma)[slice * n + list[c]] = sg;
+      }
+      // Jacobi V -> V (I1 >= I2) or U (I1 < I2); n x n
+      T* Vout = jp.transposed ? reinterpret_cast<T*>(a.io.U) + slice * I1 * I1
+                              : reinterpret_cast<T*>(a.io.V) + slice * I2 * I2;
+      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int r = idx % n, c = idx / n;
+        Vout[r + (size_t)n * list[c]] = Vj[r + (size_t)np * c];
+      }
+      // W side: m x m, Q[:, rank] = w / sigma for sigma above the rank threshold
+      T* Q = jp.transposed ? reinterpret_cast<T*>(a.io.V) + slice * I2 * I2
+                           : reinterpret_cast<T*>(a.io.U) + slice * I1 * I1;
+      const T thr = T(m) * unit_roundoff<T>() * sig_max;
+      if (threadIdx.x == 0) {
+        int nv = 0;
+        for (int c = 0; c < n; ++c) nv += sqrt(nrm[c]) > thr;
+        s_count = nv;
+      }
+      __syncthreads();
+      const int nv = s_count;
+      for (int idx = threadIdx.x; idx < m * n; idx += blockDim.x) {
+        const int r = idx % m, c = idx / m;
+        if (list[c] < nv) Q[r + (size_t)m * list[c]] = W[r + (size_t)ld * c] / sqrt(nrm[c]);
+      }
+      __syncthreads();
+      // complete Q to an orthogonal m x m basis: for each missing column take the
+      // canonical vector e_c farthest from span(Q) (its squared distance is
+      // 1 - ||Q(c, :)||^2, at least (m - q)/m for the best c) and orthogonalise it
+      // against Q twice (classical Gram-Schmidt, two passes).
+      T* v = vtmp;
+      T* cf = vtmp + m;
+      __shared__ int s_arg[kWarps];
+      __shared__ T s_val[kWarps];
+      for (int q = nv; q < m; ++q) {
+        // pick the candidate
+        T best = T(-1);
+        int bi = 0;
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+          T acc = T(1);
+          for (int j = 0; j < q; ++j) acc -= Q[r + (size_t)m * j] * Q[r + (size_t)m * j];
+          if (acc > best) { best = acc; bi = r; }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        if (lane == 0) { s_val[warp] = best; s_arg[warp] = bi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          T b = s_val[0];
+          int ix = s_arg[0];
+          for (int w = 1; w < kWarps; ++w)
+            if (s_val[w] > b || (s_val[w] == b && s_arg[w] < ix)) { b = s_val[w]; ix = s_arg[w]; }
+          s_cand = ix;
+        }
+        __syncthreads();
+        const int cand = s_cand;
+        // pass 1: v = e_cand - Q(:, :q) Q(cand, :q)^T
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+          T acc = (r == cand) ? T(1) : T(0);
+          for (int j = 0; j < q; ++j) acc -= Q[r + (size_t)m * j] * Q[cand + (size_t)m * j];
+          v[r] = acc;
+        }
+        __syncthreads();
+        // pass 2: v -= Q (Q^T v)
+        for (int j = warp; j < q; j += kWarps) {
+          T acc = T(0);
+          for (int r = lane; r < m; r += 32) acc = fma(Q[r + (size_t)m * j], v[r], acc);
+          acc = warp_allsum(acc);
+          if (lane == 0) cf[j] = acc;
+        }
+        __syncthreads();
+        T part = T(0);
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+          T acc = v[r];
+          for (int j = 0; j < q; ++j) acc -= Q[r + (size_t)m * j] * cf[j];
+          v[r] = acc;
+          part = fma(acc, acc, part);
+        }
+        part = warp_allsum(part);
+        if (lane == 0) s_red[warp] = part;
+        __syncthreads();
+        T nv2 = T(0);
+        for (int w = 0; w < kWarps; ++w) nv2 += s_red[w];
+        const T inv = T(1) / sqrt(nv2);
+        for (int r = threadIdx.x; r < m; r += blockDim.x) Q[r + (size_t)m * q] = v[r] * inv;
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+size_t smem_need(const JacobiPlan& jp) {
+  size_t b = 0;
+  if (jp.w_in_smem) b += sizeof(T) * (size_t)jp.ld * jp.npad;
+  b += sizeof(T) * jp.npad + sizeof(int) * jp.npad + sizeof(T) * (size_t)kWarps * jp.npad;
+  if (jp.mode == JAC_SVD) b += sizeof(T) * 2 * (size_t)jp.m;
+  return (b + 15) & ~size_t(15);
+}
+
+template <typename T, int E>
+cudaError_t launch_e(const JArgs& a, int grid, cudaStream_t st) {
+  auto k = jacobi_kernel<T, E>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.jp.smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kJThreads, a.jp.smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_t(const JArgs& a, int grid, cudaStream_t st) {
+  switch (a.jp.E) {
+    case 1: return launch_e<T, 1>(a, grid, st);
+    case 2: return launch_e<T, 2>(a, grid, st);
+    case 4: return launch_e<T, 4>(a, grid, st);
+    case 8: return launch_e<T, 8>(a, grid, st);
+    case 16: return launch_e<T, 16>(a, grid, st);
+    case 32: return launch_e<T, 32>(a, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int jacobi_grid(const Ctx& c, const JacobiPlan& jp) {
+  if (jp.w_in_smem && jp.mode == JAC_SVT) return (int)std::min<int64_t>(jp.P, 1 << 20);
+  // global regions are per CTA: bound the grid by what can be resident
+  return (int)std::max<int64_t>(1, std::min<int64_t>(jp.P, (int64_t)c.sms * 2));
+}
+
+}  // namespace
+
+lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan* out) {
+  JacobiPlan jp;
+  jp.mode = mode;
+  jp.I1 = I1;
+  jp.I2 = I2;
+  jp.P = c.P;
+  jp.transposed = I1 < I2;
+  jp.m = (int)std::max(I1, I2);
+  jp.n = (int)std::min(I1, I2);
+  jp.npad = jp.n + (jp.n & 1);
+  jp.ld = jp.m | 1;  // odd leading dimension: conflict-free transposed stores
+  const int maxE = c.elem == 8 ? 16 : 32;
+  int E = 1;
+  while (32 * E < jp.m) E *= 2;
+  if (E > maxE) return LT_ERR_SHAPE;  // column must fit the registers of a warp
+  jp.E = E;
+  jp.threads = kJThreads;
+  jp.w_in_smem = true;
+  size_t need = c.elem == 8 ? smem_need<double>(jp) : smem_need<float>(jp);
+  if (need > (size_t)kSmemOptin - 1024) {
+    jp.w_in_smem = false;
+    need = c.elem == 8 ? smem_need<double>(jp) : smem_need<float>(jp);
+    if (need > (size_t)kSmemOptin - 1024) return LT_ERR_SHAPE;
+  }
+  jp.smem = (int)need;
+  const int grid = jacobi_grid(c, jp);
+  size_t ws = 0;
+  if (!jp.w_in_smem) ws += (size_t)c.elem * grid * jp.ld * jp.npad;
+  if (mode == JAC_SVD) ws += (size_t)c.elem * grid * jp.npad * jp.npad;
+  jp.ws_bytes = (ws + 255) & ~size_t(255);
+  *out = jp;
+  return LT_OK;
+}
+
+cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io,
+                          cudaStream_t st) {
+  JArgs a;
+  a.jp = jp;
+  a.io = io;
+  a.max_sweeps = c.max_sweeps;
+  const double u = c.elem == 8 ? DBL_EPSILON / 2 : FLT_EPSILON / 2;
+  a.tol = c.jacobi_tol > 0 ? c.jacobi_tol
+                           : (c.elem == 8 ? jp.m * u : 4.0 * std::sqrt((double)jp.m) * u);
+  a.status = c.d_status;
+  const int grid = jacobi_grid(c, jp);
+  return c.elem == 8 ? launch_t<double>(a, grid, st) : launch_t<float>(a, grid, st);
+}
+
+}  // namespace lt

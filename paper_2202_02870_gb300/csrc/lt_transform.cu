@@ -1,0 +1,326 @@
+// Kernel T: the operator L of Sec. 3.2 (and its inverse), L(X) = X x_3 M_3 ... x_K M_K,
+// as a sequence of n-mode products (Eq. 3) applied to tiles held in shared memory.
+//
+// A pass applies a group of consecutive modes to the view [outer][Pg][Sg] of the
+// tensor (Sg = elements between consecutive indices of the pass's first mode).  A CTA
+// owns a tile of TS consecutive Sg positions of one outer block: it loads the Pg x TS
+// sub-matrix once (coalesced TS-wide rows), applies every mode of the pass in shared
+// memory (ping-pong buffers; the transform matrices are staged in shared memory and
+// read as warp-wide broadcasts), and writes the tile back.  With all modes in one
+// pass (the common case) the tensor is read and written exactly once.
+//
+// Fusions for PGA (Eqs. 51-52, Sec. 5 stopping test):
+//   FUSE_PGA_FORWARD  (first pass load)  Y = X + beta (X - X_old);
+//                                          G = Y - step * mask * (Y - obs)
+//   FUSE_PGA_INVERSE  (last pass store)  X_new -> x_out; per-CTA partial sums of
+//                                          ||Y - X_new||^2, ||X_new||^2 and, if asked,
+//                                          ||mask (X_new - obs)||^2 (FP64 across tiles)
+#include <algorithm>
+
+#include "lt_internal.cuh"
+
+namespace lt {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kR = 4;  // outputs per work item (register blocking along the mode)
+
+template <typename T>
+struct Acc;  // per-tile accumulator type of the epilogue sums
+template <>
+struct Acc<double> { using type = double; };
+template <>
+struct Acc<float> { using type = float; };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct PassArgs {
+  TransformPass p;
+  const void* in;
+  void* out;
+  const void* mats;   // base of the context's matrix array (fwd or inv)
+  PgaFuse fuse;
+  int fuse_mode;      // FUSE_* for this pass
+};
+
+template <typename T, int TS>
+__global__ void __launch_bounds__(kThreads)
+transform_kernel(const PassArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TransformPass& p = a.p;
+  if (a.fuse.scal != nullptr && a.fuse.scal->done) return;  // PGA converged earlier
+
+  const int Pg = (int)p.Pg;
+  T* buf0 = reinterpret_cast<T*>(smem_raw);
+  T* buf1 = buf0 + (size_t)Pg * TS;
+  T* mats_s = buf1 + (size_t)Pg * TS;
+
+  // Stage the pass's matrices (row-major I x I each) in shared memory.
+  int moff_s[kMaxModes];
+  {
+    int acc = 0;
+    for (int q = 0; q < p.nm; ++q) {
+      moff_s[q] = acc;
+      const T* src = reinterpret_cast<const T*>(a.mats) + p.mat_off[q];
+      const int cnt = p.msize[q] * p.msize[q];
+      for (int i = threadIdx.x; i < cnt; i += blockDim.x) mats_s[acc + i] = src[i];
+      acc += cnt;
+    }
+  }
+  __syncthreads();
+
+  const int lane_s = threadIdx.x % TS;
+  const int grp = threadIdx.x / TS;
+  const int ngrp = blockDim.x / TS;
+  const int64_t tiles_per_outer = (p.Sg + TS - 1) / TS;
+  const int64_t ntiles = p.outer * tiles_per_outer;
+  using AccT = typename Acc<T>::type;
+  double sum_r = 0.0, sum_x = 0.0, sum_f = 0.0;
+
+  const T* gin = reinterpret_cast<const T*>(a.in);
+  T* gout = reinterpret_cast<T*>(a.out);
+  const T* xc = reinterpret_cast<const T*>(a.fuse.x_cur);
+  const T* xo = reinterpret_cast<const T*>(a.fuse.x_old);
+  const T* ob = reinterpret_cast<const T*>(a.fuse.obs);
+  T* xout = reinterpret_cast<T*>(a.fuse.x_out);
+  const uint8_t* mk = a.fuse.mask;
+  T beta = T(0), step = T(a.fuse.step);
+  if (a.fuse_mode != FUSE_NONE) beta = T(a.fuse.scal->beta);
+
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t o = tile / tiles_per_outer;
+    const int64_t s0 = (tile % tiles_per_outer) * TS;
+    const int64_t base = o * p.Pg * p.Sg + s0;
+    const bool full = (s0 + TS <= p.Sg);
+
+    // ---- load (with the PGA prologue when fusing the forward transform)
+    for (int idx = threadIdx.x; idx < Pg * TS; idx += blockDim.x) {
+      const int pp = idx / TS, s = idx % TS;
+      T v = T(0);
+      if (full || s0 + s < p.Sg) {
+        const int64_t e = base + (int64_t)pp * p.Sg + s;
+        if (a.fuse_mode == FUSE_PGA_FORWARD) {
+          const T x = xc[e], x_old = xo[e];
+          const T y = x + beta * (x - x_old);
+          v = mk[e] ? y - step * (y - ob[e]) : y;
+        } else {
+          v = gin[e];
+        }
+      }
+      buf0[idx] = v;
+    }
+    __syncthreads();
+
+    // ---- mode products, one mode after the other
+    T* src = buf0;
+    T* dst = buf1;
+    for (int q = 0; q < p.nm; ++q) {
+      const int I = p.msize[q], st = p.mstride[q];
+      const T* M = mats_s + moff_s[q];
+      const int nch = (I + kR - 1) / kR;
+      const int items = (Pg / I) * nch;
+      for (int it = grp; it < items; it += ngrp) {
+        const int fiber = it / nch, ch = it % nch;
+        const int aa = fiber % st, bb = fiber / st;
+        const int fbase = aa + st * I * bb;
+        const int j0 = ch * kR;
+        T acc[kR];
+#pragma unroll
+        for (int r = 0; r < kR; ++r) acc[r] = T(0);
+        for (int i = 0; i < I; ++i) {
+          const T x = src[(fbase + st * i) * TS + lane_s];
+#pragma unroll
+          for (int r = 0; r < kR; ++r)
+            if (j0 + r < I) acc[r] = fma(M[(j0 + r) * I + i], x, acc[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < kR; ++r)
+          if (j0 + r < I) dst[(fbase + st * (j0 + r)) * TS + lane_s] = acc[r];
+      }
+      __syncthreads();
+      T* t = src; src = dst; dst = t;
+    }
+
+    // ---- store (with the PGA epilogue when fusing the inverse transform)
+    AccT tr = AccT(0), tx = AccT(0), tf = AccT(0);
+    for (int idx = threadIdx.x; idx < Pg * TS; idx += blockDim.x) {
+      const int pp = idx / TS, s = idx % TS;
+      if (!(full || s0 + s < p.Sg)) continue;
+      const int64_t e = base + (int64_t)pp * p.Sg + s;
+      const T xn = src[idx];
+      if (a.fuse_mode == FUSE_PGA_INVERSE) {
+        const T x = xc[e], x_old = xo[e];
+        const T y = x + beta * (x - x_old);
+        const T d = y - xn;
+        tr = fma(AccT(d), AccT(d), tr);
+        tx = fma(AccT(xn), AccT(xn), tx);
+        if (a.fuse.objective && mk[e]) {
+          const T f = xn - ob[e];
+          tf = fma(AccT(f), AccT(f), tf);
+        }
+        xout[e] = xn;
+      } else {
+        gout[e] = xn;
+      }
+    }
+    sum_r += double(tr);
+    sum_x += double(tx);
+    sum_f += double(tf);
+    __syncthreads();  // buffers are reused by the next tile
+  }
+
+  if (a.fuse_mode == FUSE_PGA_INVERSE) {
+    __shared__ double red[3][kThreads / 32];
+    sum_r = warp_sum(sum_r);
+    sum_x = warp_sum(sum_x);
+    sum_f = warp_sum(sum_f);
+    const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+    if (l == 0) { red[0][w] = sum_r; red[1][w] = sum_x; red[2][w] = sum_f; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r0 = 0, r1 = 0, r2 = 0;
+      for (int i = 0; i < (int)(blockDim.x / 32); ++i) { r0 += red[0][i]; r1 += red[1][i]; r2 += red[2][i]; }
+      double* out = a.fuse.partials + 4 * (size_t)blockIdx.x;
+      out[0] = r0; out[1] = r1; out[2] = r2; out[3] = 0.0;
+    }
+  }
+}
+
+template <typename T>
+size_t smem_bytes(const TransformPass& p, int ts) {
+  size_t mats = 0;
+  for (int q = 0; q < p.nm; ++q) mats += (size_t)p.msize[q] * p.msize[q];
+  return (2 * (size_t)p.Pg * ts + mats) * sizeof(T);
+}
+
+template <typename T, int TS>
+cudaError_t launch_pass_t(const Ctx& c, const PassArgs& a, int grid, cudaStream_t st) {
+  auto k = transform_kernel<T, TS>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.p.smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, kThreads, a.p.smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_pass(const Ctx& c, const PassArgs& a, int grid, cudaStream_t st) {
+  switch (a.p.ts) {
+    case 32: return launch_pass_t<T, 32>(c, a, grid, st);
+    case 16: return launch_pass_t<T, 16>(c, a, grid, st);
+    case 8: return launch_pass_t<T, 8>(c, a, grid, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T, int TS>
+int occupancy(const TransformPass& p) {
+  int nb = 0;
+  cudaFuncSetAttribute(transform_kernel<T, TS>, cudaFuncAttributeMaxDynamicSharedMemorySize, p.smem);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, transform_kernel<T, TS>, kThreads, p.smem) != cudaSuccess)
+    nb = 1;
+  return std::max(nb, 1);
+}
+
+template <typename T>
+int occupancy_t(const TransformPass& p) {
+  switch (p.ts) {
+    case 32: return occupancy<T, 32>(p);
+    case 16: return occupancy<T, 16>(p);
+    default: return occupancy<T, 8>(p);
+  }
+}
+
+}  // namespace
+
+int transform_grid(const Ctx& c, const TransformPass& p) {
+  const int per_sm = c.elem == 8 ? occupancy_t<double>(p) : occupancy_t<float>(p);
+  const int64_t tiles = p.outer * ((p.Sg + p.ts - 1) / p.ts);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)c.sms * per_sm));
+}
+
+lt_status plan_transform(const Ctx& c, int64_t S, bool inverse, TransformPlan* plan) {
+  // Application order: forward 3..K, inverse K..3 (Sec. 3.2).  The modes of a pass
+  // must be consecutive in memory, so a pass is a contiguous index range [k0, k1) of
+  // 0-based modes; for the inverse the ranges are visited from the last mode down and
+  // each pass applies its modes from its highest to its lowest.
+  const int nm = c.nmodes;
+  const size_t budget = 200 * 1024;
+  TransformPlan pl;
+  pl.inverse = inverse;
+  int k = inverse ? nm - 1 : 0;
+  while (inverse ? k >= 0 : k < nm) {
+    // grow the group [lo, hi] while it fits
+    int lo = k, hi = k;
+    auto fits = [&](int l, int h, int ts) {
+      TransformPass t;
+      t.nm = h - l + 1;
+      t.Pg = 1;
+      for (int q = l; q <= h; ++q) { t.msize[q - l] = (int)c.sizes[q]; t.Pg *= c.sizes[q]; }
+      return (c.elem == 8 ? smem_bytes<double>(t, ts) : smem_bytes<float>(t, ts)) <= budget &&
+             t.Pg <= (1 << 20);
+    };
+    int ts = 32;
+    while (ts >= 8 && !fits(lo, hi, ts)) ts /= 2;
+    if (ts < 8) return LT_ERR_SHAPE;  // one mode alone too large
+    for (;;) {
+      int nlo = inverse ? lo - 1 : lo, nhi = inverse ? hi : hi + 1;
+      if (nlo < 0 || nhi >= nm) break;
+      if (fits(nlo, nhi, 32)) { lo = nlo; hi = nhi; continue; }
+      break;
+    }
+    // TS: widest that fits
+    ts = 32;
+    while (ts > 8 && !fits(lo, hi, ts)) ts /= 2;
+    TransformPass& ps = pl.pass[pl.npass++];
+    ps.nm = hi - lo + 1;
+    ps.ts = ts;
+    int64_t before = 1, inside = 1, after = 1;
+    for (int q = 0; q < lo; ++q) before *= c.sizes[q];
+    for (int q = lo; q <= hi; ++q) inside *= c.sizes[q];
+    for (int q = hi + 1; q < nm; ++q) after *= c.sizes[q];
+    ps.Pg = inside;
+    ps.Sg = S * before;
+    ps.outer = after;
+    // modes in application order with their stride inside Pg
+    for (int j = 0; j < ps.nm; ++j) {
+      const int q = inverse ? hi - j : lo + j;
+      int64_t stride = 1;
+      for (int r = lo; r < q; ++r) stride *= c.sizes[r];
+      ps.msize[j] = (int)c.sizes[q];
+      ps.mstride[j] = (int)stride;
+      ps.mat_off[j] = c.mat_off[q];
+    }
+    ps.smem = (int)(c.elem == 8 ? smem_bytes<double>(ps, ts) : smem_bytes<float>(ps, ts));
+    k = inverse ? lo - 1 : hi + 1;
+  }
+  *plan = pl;
+  return LT_OK;
+}
+
+cudaError_t launch_transform(const Ctx& c, const TransformPlan& plan, const void* in,
+                             void* out, int fuse_mode, const PgaFuse* fuse,
+                             cudaStream_t st, int* grid_out) {
+  for (int i = 0; i < plan.npass; ++i) {
+    PassArgs a;
+    a.p = plan.pass[i];
+    a.in = (i == 0) ? in : out;
+    a.out = out;
+    a.mats = plan.inverse ? c.d_inv : c.d_fwd;
+    a.fuse_mode = FUSE_NONE;
+    if (fuse) a.fuse = *fuse;
+    if (fuse_mode == FUSE_PGA_FORWARD && i == 0) a.fuse_mode = FUSE_PGA_FORWARD;
+    if (fuse_mode == FUSE_PGA_INVERSE && i == plan.npass - 1) a.fuse_mode = FUSE_PGA_INVERSE;
+    const int grid = transform_grid(c, a.p);
+    if (grid_out) *grid_out = grid;
+    const cudaError_t e = (c.elem == 8) ? launch_pass<double>(c, a, grid, st)
+                                        : launch_pass<float>(c, a, grid, st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace lt

@@ -1,0 +1,333 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element
+on the same seeded inputs.
+
+Tolerances (relative Frobenius error against the oracle):
+  FP64 path: 1e-12 (orthonormal or moderately conditioned L).
+  FP32 path: 1e-5 -- single precision with unit roundoff 6e-8; transforms of size
+             I accumulate ~sqrt(I) u of relative error per mode, the Jacobi SVT stops at
+             4 sqrt(m) u pair orthogonality, and both stay well inside 1e-5 at the
+             sizes tested.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import definitions as Def
+from oracle import lt_oracle as O
+from paper_2202_02870_gb300 import lt, synth
+from tests.gpu_util import (dtype_of, empty_dev, from_dev, make_ctx, oracle_mats, rel,
+                            to_dev)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {lt.LT_FP64: 1e-12, lt.LT_FP32: 1e-5}
+PRECS = [lt.LT_FP64, lt.LT_FP32]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2202_02870_gb300 import build
+    build.build()
+    torch.cuda.init()
+
+
+def random_transforms(rng, sizes, cond=10.0):
+    return [("matrix", synth.conditioned_matrix(rng, n, cond, two_sided=True)) for n in sizes]
+
+
+# ------------------------------------------------------------------ transforms
+TRANSFORM_CASES = [
+    ((32, 24), [("dct", 8)]),
+    ((5, 7), [("dct", 3), ("dct", 4)]),
+    ((1, 1), [("dct", 2), ("dct", 3), ("dct", 2)]),
+    ((13, 9), [("dct", 1)]),
+    ((33, 3), "random3"),
+    ((3, 5), [("dct", 16), ("dct", 16), ("dct", 8)]),     # P = 2048: grouped passes
+    ((7, 6), [("dct", 120)]),
+]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape,transforms", TRANSFORM_CASES)
+def test_transform_and_inverse(prec, shape, transforms):
+    rng = np.random.default_rng(100 + shape[0])
+    if transforms == "random3":
+        transforms = random_transforms(rng, (4, 3, 5))
+    full = tuple(shape) + tuple(
+        t[1] if t[0] == "dct" else np.asarray(t[1]).shape[0] for t in transforms)
+    X = rng.uniform(-1, 1, size=full)
+    Ms = oracle_mats(transforms)
+    ctx = make_ctx(transforms, prec)
+    dt = dtype_of(prec)
+    Xd = to_dev(X, dt)
+    Xh = empty_dev(full, dt)
+    lt.lt_transform(ctx, Xd, Xh)
+    Xb = empty_dev(full, dt)
+    lt.lt_inverse(ctx, Xh, Xb)
+    torch.cuda.synchronize()
+    assert rel(from_dev(Xh, full), O.transform(X, Ms)) <= TOL[prec]
+    assert rel(from_dev(Xb, full), X) <= TOL[prec] * 10
+    # in place
+    lt.lt_transform(ctx, Xd, Xd)
+    torch.cuda.synchronize()
+    assert rel(from_dev(Xd, full), O.transform(X, Ms)) <= TOL[prec]
+
+
+# ------------------------------------------------------------------ products
+@pytest.mark.parametrize("prec", PRECS)
+def test_product_config1(prec):
+    """*_L-product of the 32x24x8 and 24x16x8 operands (DCT-II 8)."""
+    c = synth.config1()
+    Ms = oracle_mats(c["transforms"])
+    ctx = make_ctx(c["transforms"], prec)
+    dt = dtype_of(prec)
+    A, B = to_dev(c["A"], dt), to_dev(c["B"], dt)
+    Cd = empty_dev((32, 16, 8), dt)
+    lt.lt_product(ctx, A, B, Cd)
+    torch.cuda.synchronize()
+    assert rel(from_dev(Cd, (32, 16, 8)), O.product(c["A"], c["B"], Ms)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("shapes", [((3, 2, 4), (2, 3, 4)), ((2, 3, 3, 2), (3, 2, 3, 2)),
+                                    ((4, 2, 2, 3, 2), (2, 5, 2, 3, 2))])
+def test_product_equals_cproduct_definition(shapes):
+    """With M = W^{-1} C (I+Z) from lt_make_cproduct on every mode the GPU product is
+    the generalized c-product ten(btph(A) btph(B)) of Def. 9."""
+    rng = np.random.default_rng(7)
+    A, B = rng.standard_normal(shapes[0]), rng.standard_normal(shapes[1])
+    tr = [("cprod", n) for n in shapes[0][2:]]
+    ctx = make_ctx(tr)
+    Cshape = (shapes[0][0], shapes[1][1]) + tuple(shapes[0][2:])
+    Cd = empty_dev(Cshape)
+    lt.lt_product(ctx, to_dev(A), to_dev(B), Cd)
+    torch.cuda.synchronize()
+    assert rel(from_dev(Cd, Cshape), Def.cproduct_def(A, B)) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("I1,l,I2,trailing", [(65, 17, 70, (3,)), (1, 1, 1, (2, 2)),
+                                              (130, 64, 129, (2, 3))])
+def test_product_ragged_tiles(prec, I1, l, I2, trailing):
+    rng = np.random.default_rng(I1 + l + I2)
+    A = rng.uniform(-1, 1, (I1, l) + trailing)
+    B = rng.uniform(-1, 1, (l, I2) + trailing)
+    tr = random_transforms(rng, trailing)
+    ctx = make_ctx(tr, prec)
+    dt = dtype_of(prec)
+    Cd = empty_dev((I1, I2) + trailing, dt)
+    lt.lt_product(ctx, to_dev(A, dt), to_dev(B, dt), Cd)
+    torch.cuda.synchronize()
+    assert rel(from_dev(Cd, (I1, I2) + trailing), O.product(A, B, oracle_mats(tr))) <= TOL[prec] * 10
+
+
+# ------------------------------------------------------------------ SVD
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape,transforms", [((32, 24), [("dct", 8)]), ((24, 32), [("dct", 8)]),
+                                              ((7, 7), [("dct", 3), ("dct", 2)]),
+                                              ((9, 4), "random2")])
+def test_svd_invariants(prec, shape, transforms):
+    """Theorem of Eq. tsvd1: A = U * S * V^T, L(U)^p and L(V)^p orthogonal, L(S)^p
+    diagonal with the oracle's singular values (descending).  Vectors are not unique,
+    so they are checked through these invariants."""
+    rng = np.random.default_rng(shape[0] * 31 + shape[1])
+    if transforms == "random2":
+        transforms = random_transforms(rng, (3, 2))
+    if shape == (32, 24):
+        A = synth.config1()["A"]
+    else:
+        trailing = tuple(t[1] if t[0] == "dct" else np.asarray(t[1]).shape[0] for t in transforms)
+        A = rng.uniform(-1, 1, tuple(shape) + trailing)
+    trailing = A.shape[2:]
+    Ms = oracle_mats(transforms)
+    ctx = make_ctx(transforms, prec)
+    dt = dtype_of(prec)
+    I1, I2 = shape
+    P = int(np.prod(trailing))
+    U, S, V = empty_dev((I1, I1) + trailing, dt), empty_dev((I1, I2) + trailing, dt), \
+        empty_dev((I2, I2) + trailing, dt)
+    sig = torch.empty((P, min(I1, I2)), dtype=dt, device="cuda")
+    lt.lt_svd(ctx, to_dev(A, dt), U, S, V, sigma=sig)
+    torch.cuda.synchronize()
+    Uh, Sh, Vh = (from_dev(t, s) for t, s in ((U, (I1, I1) + trailing), (S, (I1, I2) + trailing),
+                                                (V, (I2, I2) + trailing)))
+    tol = TOL[prec] * 100
+    rec = O.product(O.product(Uh, Sh, Ms), O.transpose(Vh, Ms), Ms)
+    assert rel(rec, A) <= tol
+    _, _, _, sig_ref = O.svd(A, Ms)
+    assert rel(sig.double().cpu().numpy().T, sig_ref) <= tol
+    Lu, Ls, Lv = (O.slices(O.transform(T, Ms)) for T in (Uh, Sh, Vh))
+    for p in range(P):
+        assert np.abs(Lu[:, :, p].T @ Lu[:, :, p] - np.eye(I1)).max() <= tol * 10
+        assert np.abs(Lv[:, :, p].T @ Lv[:, :, p] - np.eye(I2)).max() <= tol * 10
+        off = Ls[:, :, p].copy()
+        np.fill_diagonal(off, 0)
+        assert np.abs(off).max() <= tol * np.abs(Ls).max()
+
+
+# ------------------------------------------------------------------ SVT
+SVT_CASES = [((32, 24), [("dct", 8)], 0.5), ((24, 32), [("dct", 8)], 0.5),
+             ((17, 17), [("dct", 3), ("dct", 4)], 0.3), ((144, 176), [("dct", 3)], 2.0),
+             ((176, 144), [("dct", 2)], 2.0), ((5, 31), "random2", 0.1),
+             ((40, 9), [("dct", 2)], 0.0), ((8, 6), [("dct", 2)], 1e6)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("shape,transforms,tau", SVT_CASES)
+def test_svt(prec, shape, transforms, tau):
+    rng = np.random.default_rng(shape[0] + 1000 * shape[1])
+    if transforms == "random2":
+        transforms = random_transforms(rng, (2, 3))
+    trailing = tuple(t[1] if t[0] == "dct" else np.asarray(t[1]).shape[0] for t in transforms)
+    full = tuple(shape) + trailing
+    A = synth.config1()["A"] if full == (32, 24, 8) else rng.standard_normal(full)
+    Ms = oracle_mats(transforms)
+    ctx = make_ctx(transforms, prec)
+    dt = dtype_of(prec)
+    Ad = to_dev(A, dt)
+    D = empty_dev(full, dt)
+    lt.lt_svt(ctx, Ad, tau, D)
+    torch.cuda.synchronize()
+    ref = O.svt(A, tau, Ms)
+    if np.linalg.norm(ref) == 0:
+        assert np.abs(from_dev(D, full)).max() <= TOL[prec] * np.abs(A).max()
+    else:
+        assert rel(from_dev(D, full), ref) <= TOL[prec]
+    # in place (D aliases A)
+    lt.lt_svt(ctx, Ad, tau, Ad)
+    torch.cuda.synchronize()
+    if np.linalg.norm(ref) > 0:
+        assert rel(from_dev(Ad, full), ref) <= TOL[prec]
+    assert lt.lt_last_device_status(ctx) == 0
+
+
+# ------------------------------------------------------------------ PGA
+def completion_inputs(c):
+    Ms = oracle_mats(c["transforms"])
+    X = O.product(c["U"], O.transpose(c["V"], Ms), Ms)
+    obs = c["mask"] * (X + c["noise"])
+    return X, obs, Ms
+
+
+def run_pga(c, obs, prec, iters, tol=0.0, X0=None, state=None):
+    ctx = make_ctx(c["transforms"], prec)
+    dt = dtype_of(prec)
+    shape = obs.shape
+    X = to_dev(np.zeros(shape) if X0 is None else X0, dt)
+    rep = lt.lt_pga_report()
+    lt.lt_pga_complete(ctx, to_dev(c["mask"]), to_dev(obs, dt), c["tau"], c["step"], iters, X,
+                       tol=tol, report=rep, state=state)
+    torch.cuda.synchronize()
+    return X, rep, ctx
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pga_small(prec):
+    c = synth.completion_case(20, 24, 20, (3, 4), rank=3, rho=0.4)
+    c.update(tau=0.3, step=1.0)
+    Xt, obs, Ms = completion_inputs(c)
+    X, rep, _ = run_pga(c, obs, prec, 25)
+    ref, info = O.pga(c["mask"], obs, 0.3, 1.0, 25, Ms)
+    assert rep.iters_done == 25
+    assert rel(from_dev(X, obs.shape), ref) <= TOL[prec]
+    assert abs(rep.rel_residual - info["residual"][-1]) <= 1e-8 + TOL[prec] * 10
+
+
+def test_pga_step_and_tolerance_stop():
+    c = synth.completion_case(21, 18, 26, (2, 3), rank=2, rho=0.6)
+    c.update(tau=0.05, step=0.7)
+    Xt, obs, Ms = completion_inputs(c)
+    X, rep, _ = run_pga(c, obs, lt.LT_FP64, 300, tol=1e-5)
+    ref, info = O.pga(c["mask"], obs, 0.05, 0.7, 300, Ms, tol=1e-5)
+    assert rep.iters_done == info["iters"] < 300
+    assert rel(from_dev(X, obs.shape), ref) <= 1e-12
+
+
+def test_pga_resume_is_bitwise():
+    """50 + 50 iterations through the checkpoint state equal 100 in one call, bit for bit
+    (fixed-order reductions)."""
+    c = synth.completion_case(22, 16, 12, (3, 2), rank=2, rho=0.5)
+    c.update(tau=0.2, step=1.0)
+    _, obs, _ = completion_inputs(c)
+    Xa, _, _ = run_pga(c, obs, lt.LT_FP64, 100)
+    ctx = make_ctx(c["transforms"])
+    Xb = to_dev(np.zeros(obs.shape))
+    prev = torch.zeros_like(Xb)
+    st = lt.lt_pga_state(X_prev=prev.data_ptr(), t_prev=1.0, t=1.0, k=0)
+    m, o = to_dev(c["mask"]), to_dev(obs)
+    lt.lt_pga_complete(ctx, m, o, 0.2, 1.0, 50, Xb, state=st)
+    torch.cuda.synchronize()
+    assert st.k == 50
+    lt.lt_pga_complete(ctx, m, o, 0.2, 1.0, 50, Xb, state=st)
+    torch.cuda.synchronize()
+    assert st.k == 100
+    assert torch.equal(Xa, Xb)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pga_config2_full(prec):
+    """The benchmarked workload at full size: 144x176x3x32, L-rank 10, 30% observed,
+    DCT 3 / DCT 32, tau 0.5, step 1, 100 iterations."""
+    c = synth.config2()
+    Xt, obs, Ms = completion_inputs(c)
+    X, rep, _ = run_pga(c, obs, prec, c["iters"])
+    ref, info = O.pga(c["mask"], obs, c["tau"], c["step"], c["iters"], Ms)
+    got = from_dev(X, obs.shape)
+    assert rep.iters_done == 100
+    assert rep.device_status == 0
+    assert rel(got, ref) <= (1e-12 if prec == lt.LT_FP64 else 1e-5)
+    # sanity of the completion itself (not parity): the low-rank truth is recovered
+    assert O.rse(Xt, ref) < 0.05
+
+
+# ------------------------------------------------------------------ boundary
+def test_argument_errors_enqueue_nothing():
+    ctx = make_ctx([("dct", 4)])
+    x = torch.zeros((4, 3, 2), dtype=torch.float64, device="cuda")
+    L = lt.lib()
+    s = torch.cuda.current_stream().cuda_stream
+    assert L.lt_transform(None, 2, 3, x.data_ptr(), x.data_ptr(), None, 0, s) == -1
+    assert L.lt_transform(ctx.handle, 0, 3, x.data_ptr(), x.data_ptr(), None, 0, s) == -1
+    assert L.lt_svt(ctx.handle, 2, 3, x.data_ptr(), -1.0, x.data_ptr(), None, 0, s) == -1
+    need = lt.lt_workspace_size(ctx, lt.LT_OP_PGA, 2, 3)
+    assert need > 0
+    m = torch.zeros((4, 3, 2), dtype=torch.uint8, device="cuda")
+    assert L.lt_pga_complete(ctx.handle, 2, 3, m.data_ptr(), x.data_ptr(), 0.1, 1.0, 5, 0.0,
+                             x.data_ptr(), None, None, None, 0, s) == -8
+    assert L.lt_pga_complete(ctx.handle, 2, 3, m.data_ptr(), x.data_ptr(), 0.1, 0.0, 5, 0.0,
+                             x.data_ptr(), None, None, None, 0, s) == -1
+    sing = np.zeros((3, 3))
+    with pytest.raises(lt.LtError) as e:
+        lt.Context([3], [sing])
+    assert e.value.status == -3
+    with pytest.raises(lt.LtError):
+        lt.lt_ctx_set_option(ctx, lt.LT_OPT_MAX_SWEEPS, 0)
+
+
+def test_device_status_noconv_and_nonfinite():
+    ctx = make_ctx([("dct", 2)])
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((20, 12, 2))
+    D = empty_dev(A.shape)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_MAX_SWEEPS, 1)
+    lt.lt_svt(ctx, to_dev(A), 0.1, D)
+    st = lt.lt_last_device_status(ctx)
+    assert st & lt.LT_DEV_NOCONV
+    assert np.all(np.isfinite(from_dev(D, A.shape)))
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_MAX_SWEEPS, 40)
+    A[3, 4, 1] = np.nan
+    lt.lt_svt(ctx, to_dev(A), 0.1, D)
+    assert lt.lt_last_device_status(ctx) & lt.LT_DEV_NONFINITE
+    assert lt.lt_last_device_status(ctx) == 0  # read-and-clear
+
+
+def test_host_helpers_match_golden_and_oracle():
+    from tests.conftest import load_golden_matrices
+    g = load_golden_matrices()
+    for n in (2, 3):
+        assert np.allclose(lt.lt_make_dct(n), g[("dct", n)], atol=1e-15)
+        assert np.allclose(lt.lt_make_cproduct(n), g[("cprod", n)], atol=1e-14)
+    for n in (1, 5, 32, 120):
+        assert np.abs(lt.lt_make_dct(n) - O.dct_matrix(n)).max() < 1e-14
+        assert np.abs(lt.lt_make_cproduct(n) - O.cproduct_matrix(n)).max() < 1e-11
