@@ -83,9 +83,28 @@ typedef enum {
   LT_OPT_MAX_SWEEPS = 0,     /* Jacobi sweep limit (default 40); NOCONV when hit */
   LT_OPT_JACOBI_TOL = 1,     /* pair tolerance: rotate when |a.b| > tol*sqrt(a.a b.b);
                                 value <= 0 restores the default (m * unit roundoff for
-                                LT_FP64, 4 * sqrt(m) * unit roundoff otherwise) */
-  LT_OPT_OBJECTIVE = 2       /* PGA: also accumulate the objective (0/1, default 0) */
+                                LT_FP64, sqrt(m) * unit roundoff otherwise) */
+  LT_OPT_OBJECTIVE = 2,      /* PGA: also accumulate the objective (0/1, default 0) */
+  LT_OPT_PROFILE = 3         /* 1: bracket every kernel launch with CUDA events on its
+                                stream, summed per kernel family by lt_ctx_get_stats */
 } lt_option;
+
+/* Kernel families counted by lt_ctx_get_stats. */
+typedef enum { LT_K_TRANSFORM = 0, LT_K_JACOBI = 1, LT_K_GEMM = 2, LT_K_AUX = 3 } lt_kernel;
+
+typedef struct {
+  int64_t launches;  /* kernels of the family enqueued */
+  double ms;         /* summed CUDA-event durations (LT_OPT_PROFILE on), else 0 */
+  double flops;      /* algorithmic floating-point operations: transforms 2 N sum_k I_k
+                        per pass set; GEMM 2 M N K P; Jacobi counted by the kernel from
+                        the pairs it visited (2m), rotations it applied (6m, + 6n for V),
+                        norm passes (2mn) and the SVT reconstruction (4kmn) */
+  double bytes;      /* algorithmic DRAM bytes: each tensor read or written once */
+} lt_kernel_stats;
+
+typedef struct {
+  lt_kernel_stats k[4];
+} lt_stats;
 
 typedef struct lt_ctx_s* lt_ctx;
 
@@ -213,6 +232,11 @@ LT_API lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const in
                                   const double* step, int64_t iters, void* const* X,
                                   lt_pga_report* reports, void* ws, size_t ws_bytes,
                                   void* stream);
+
+/* Counters of the context since creation or the last reset (reset != 0 clears them
+ * after reading).  Synchronises the device when LT_OPT_PROFILE is on or when Jacobi
+ * flops are pending.  out: host. */
+LT_API lt_status lt_ctx_get_stats(lt_ctx ctx, lt_stats* out, int reset);
 
 /* Device status word of the context: OR of LT_DEV_* bits raised since the previous
  * call of this function (read and cleared).  Synchronises the device. out: host. */

@@ -96,6 +96,70 @@ lt_status check_dims(int64_t a, int64_t b) {
   return LT_OK;
 }
 
+// ---- launch accounting (lt_ctx_get_stats) ---------------------------------------------
+cudaEvent_t take_event(Ctx& c) {
+  if (!c.pool.empty()) {
+    cudaEvent_t e = c.pool.back();
+    c.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets a group of launches of one kernel family.  Counts launches and algorithmic
+// flops/bytes on the host; with LT_OPT_PROFILE records CUDA events on the stream.
+struct Scope {
+  Ctx& c;
+  cudaStream_t st;
+  int fam;
+  cudaEvent_t a = nullptr;
+  Scope(Ctx& ctx, cudaStream_t s, int f) : c(ctx), st(s), fam(f) {
+    if (c.profile) {
+      a = take_event(c);
+      cudaEventRecord(a, st);
+    }
+  }
+  void done(int64_t launches, double flops, double bytes) {
+    c.stats.k[fam].launches += launches;
+    c.stats.k[fam].flops += flops;
+    c.stats.k[fam].bytes += bytes;
+    if (c.profile && a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, st);
+      c.pending.push_back({a, b, fam});
+      a = nullptr;
+    }
+  }
+};
+
+double transform_flops(const lt::TransformPlan& p, int64_t S, int64_t P) {
+  double sum = 0;
+  for (int i = 0; i < p.npass; ++i)
+    for (int q = 0; q < p.pass[i].nm; ++q) sum += p.pass[i].msize[q];
+  return 2.0 * (double)S * (double)P * sum;
+}
+
+// One transform call: each pass reads and writes the tensor once.
+cudaError_t run_transform(Ctx& c, const lt::TransformPlan& plan, int64_t S, const void* in,
+                          void* out, cudaStream_t st) {
+  Scope sc(c, st, LT_K_TRANSFORM);
+  cudaError_t e = lt::launch_transform(c, plan, in, out, lt::FUSE_NONE, nullptr, st, nullptr);
+  sc.done(plan.npass, transform_flops(plan, S, c.P), 2.0 * plan.npass * S * c.P * c.elem);
+  return e;
+}
+
+cudaError_t run_jacobi(Ctx& c, const lt::JacobiPlan& jp, lt::JacobiIO io, cudaStream_t st) {
+  Scope sc(c, st, LT_K_JACOBI);
+  io.flops = c.d_counters + LT_K_JACOBI;
+  cudaError_t e = lt::launch_jacobi(c, jp, io, st);
+  // bytes: read the slices, re-read them for the reconstruction, write the result
+  const double n = (double)jp.I1 * jp.I2 * c.P * c.elem;
+  sc.done(1, 0.0, jp.mode == lt::JAC_SVT ? 3 * n : 2 * n);
+  return e;
+}
+
 // ---- workspace layouts ---------------------------------------------------------------
 struct PgaLayout {
   size_t x2, ghat, partials, scal, info, jac, total;
@@ -245,6 +309,8 @@ lt_status lt_ctx_create(int K, const int64_t* mode_sizes, const double* const* M
   if (e == cudaSuccess) e = cudaMemcpy(c->d_inv, bi.data(), bi.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, sizeof(lt::PgaScalars));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 4 * sizeof(double));
   if (e != cudaSuccess) { lt_ctx_destroy(reinterpret_cast<lt_ctx>(c)); return LT_ERR_CUDA; }
   *out = reinterpret_cast<lt_ctx>(c);
   return LT_OK;
@@ -258,6 +324,9 @@ lt_status lt_ctx_destroy(lt_ctx ctx) {
   if (c->d_inv) cudaFree(c->d_inv);
   if (c->d_status) cudaFree(c->d_status);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
+  if (c->d_counters) cudaFree(c->d_counters);
+  for (auto& r : c->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto ev : c->pool) cudaEventDestroy(ev);
   delete c;
   return LT_OK;
 }
@@ -276,6 +345,9 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
       return LT_OK;
     case LT_OPT_OBJECTIVE:
       c->objective = value != 0.0;
+      return LT_OK;
+    case LT_OPT_PROFILE:
+      c->profile = value != 0.0;
       return LT_OK;
   }
   return LT_ERR_ARG;
@@ -331,12 +403,11 @@ lt_status lt_transform(lt_ctx ctx, int64_t I1, int64_t I2, const void* X, void* 
   if (check_ctx(ctx) != LT_OK || !X || !X_hat) return LT_ERR_ARG;
   lt_status s = check_dims(I1, I2);
   if (s != LT_OK) return s;
-  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   lt::TransformPlan plan;
   s = lt::plan_transform(c, I1 * I2, false, &plan);
   if (s != LT_OK) return s;
-  return cuda_status(lt::launch_transform(c, plan, X, X_hat, lt::FUSE_NONE, nullptr,
-                                          (cudaStream_t)stream, nullptr));
+  return cuda_status(run_transform(c, plan, I1 * I2, X, X_hat, (cudaStream_t)stream));
 }
 
 lt_status lt_inverse(lt_ctx ctx, int64_t I1, int64_t I2, const void* X_hat, void* X,
@@ -345,12 +416,11 @@ lt_status lt_inverse(lt_ctx ctx, int64_t I1, int64_t I2, const void* X_hat, void
   if (check_ctx(ctx) != LT_OK || !X || !X_hat) return LT_ERR_ARG;
   lt_status s = check_dims(I1, I2);
   if (s != LT_OK) return s;
-  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   lt::TransformPlan plan;
   s = lt::plan_transform(c, I1 * I2, true, &plan);
   if (s != LT_OK) return s;
-  return cuda_status(lt::launch_transform(c, plan, X_hat, X, lt::FUSE_NONE, nullptr,
-                                          (cudaStream_t)stream, nullptr));
+  return cuda_status(run_transform(c, plan, I1 * I2, X_hat, X, (cudaStream_t)stream));
 }
 
 lt_status lt_product(lt_ctx ctx, int64_t I1, int64_t l, int64_t I2, const void* A,
@@ -360,7 +430,7 @@ lt_status lt_product(lt_ctx ctx, int64_t I1, int64_t l, int64_t I2, const void* 
   lt_status s = check_dims(I1, l);
   if (s == LT_OK) s = check_dims(l, I2);
   if (s != LT_OK) return s;
-  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   size_t need = 0;
   s = lt_workspace_size(ctx, LT_OP_PRODUCT, I1, l, I2, &need);
   if (s != LT_OK) return s;
@@ -374,10 +444,14 @@ lt_status lt_product(lt_ctx ctx, int64_t I1, int64_t l, int64_t I2, const void* 
   unsigned char* w = static_cast<unsigned char*>(ws);
   void* Ah = w;
   void* Bh = w + align256((size_t)I1 * l * c.P * c.elem);
-  cudaError_t e = lt::launch_transform(c, pa, A, Ah, lt::FUSE_NONE, nullptr, st, nullptr);
-  if (e == cudaSuccess) e = lt::launch_transform(c, pb, B, Bh, lt::FUSE_NONE, nullptr, st, nullptr);
-  if (e == cudaSuccess) e = lt::launch_facewise_gemm(c, I1, I2, l, Ah, Bh, C, st);
-  if (e == cudaSuccess) e = lt::launch_transform(c, pc, C, C, lt::FUSE_NONE, nullptr, st, nullptr);
+  cudaError_t e = run_transform(c, pa, I1 * l, A, Ah, st);
+  if (e == cudaSuccess) e = run_transform(c, pb, l * I2, B, Bh, st);
+  if (e == cudaSuccess) {
+    Scope sc(c, st, LT_K_GEMM);
+    e = lt::launch_facewise_gemm(c, I1, I2, l, Ah, Bh, C, st);
+    sc.done(1, 2.0 * I1 * I2 * l * c.P, (double)(I1 * l + l * I2 + I1 * I2) * c.P * c.elem);
+  }
+  if (e == cudaSuccess) e = run_transform(c, pc, I1 * I2, C, C, st);
   return cuda_status(e);
 }
 
@@ -386,7 +460,7 @@ lt_status lt_svd(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, void* U, voi
   if (check_ctx(ctx) != LT_OK || !A || !U || !S || !V) return LT_ERR_ARG;
   lt_status s = check_dims(I1, I2);
   if (s != LT_OK) return s;
-  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   size_t need = 0;
   if ((s = lt_workspace_size(ctx, LT_OP_SVD, I1, I2, 0, &need)) != LT_OK) return s;
   if ((s = check_ws(ws, ws_bytes, need)) != LT_OK) return s;
@@ -407,11 +481,11 @@ lt_status lt_svd(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, void* U, voi
   io.V = V;
   io.sigma = sigma;
   io.scratch = w + align256((size_t)I1 * I2 * c.P * c.elem);
-  cudaError_t e = lt::launch_transform(c, pa, A, Ah, lt::FUSE_NONE, nullptr, st, nullptr);
-  if (e == cudaSuccess) e = lt::launch_jacobi(c, jp, io, st);
-  if (e == cudaSuccess) e = lt::launch_transform(c, pu, U, U, lt::FUSE_NONE, nullptr, st, nullptr);
-  if (e == cudaSuccess) e = lt::launch_transform(c, ps, S, S, lt::FUSE_NONE, nullptr, st, nullptr);
-  if (e == cudaSuccess) e = lt::launch_transform(c, pv, V, V, lt::FUSE_NONE, nullptr, st, nullptr);
+  cudaError_t e = run_transform(c, pa, I1 * I2, A, Ah, st);
+  if (e == cudaSuccess) e = run_jacobi(c, jp, io, st);
+  if (e == cudaSuccess) e = run_transform(c, pu, I1 * I1, U, U, st);
+  if (e == cudaSuccess) e = run_transform(c, ps, I1 * I2, S, S, st);
+  if (e == cudaSuccess) e = run_transform(c, pv, I2 * I2, V, V, st);
   return cuda_status(e);
 }
 
@@ -421,7 +495,7 @@ lt_status lt_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau, 
   if (!(tau >= 0.0) || !std::isfinite(tau)) return LT_ERR_ARG;
   lt_status s = check_dims(I1, I2);
   if (s != LT_OK) return s;
-  const Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
   size_t need = 0;
   if ((s = lt_workspace_size(ctx, LT_OP_SVT, I1, I2, 0, &need)) != LT_OK) return s;
   if ((s = check_ws(ws, ws_bytes, need)) != LT_OK) return s;
@@ -436,9 +510,9 @@ lt_status lt_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau, 
   io.D = D;
   io.tau = tau;
   io.scratch = ws;
-  cudaError_t e = lt::launch_transform(c, pf, A, D, lt::FUSE_NONE, nullptr, st, nullptr);
-  if (e == cudaSuccess) e = lt::launch_jacobi(c, jp, io, st);
-  if (e == cudaSuccess) e = lt::launch_transform(c, pi, D, D, lt::FUSE_NONE, nullptr, st, nullptr);
+  cudaError_t e = run_transform(c, pf, I1 * I2, A, D, st);
+  if (e == cudaSuccess) e = run_jacobi(c, jp, io, st);
+  if (e == cudaSuccess) e = run_transform(c, pi, I1 * I2, D, D, st);
   return cuda_status(e);
 }
 
@@ -466,10 +540,16 @@ lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8_t* mas
   lt::SliceInfo* info = reinterpret_cast<lt::SliceInfo*>(w + L.info);
 
   const bool resume = state && state->k > 0;
-  cudaError_t e = lt::launch_copy_bytes(X2, resume ? state->X_prev : X, bytes, st);
-  if (e == cudaSuccess)
-    e = lt::launch_pga_init(scal, resume ? state->t_prev : 1.0, resume ? state->t : 1.0,
-                            resume ? state->k : 0, tol, st);
+  const double Nd = (double)I1 * I2 * c.P;
+  cudaError_t e;
+  {
+    Scope sc(c, st, LT_K_AUX);
+    e = lt::launch_copy_bytes(X2, resume ? state->X_prev : X, bytes, st);
+    if (e == cudaSuccess)
+      e = lt::launch_pga_init(scal, resume ? state->t_prev : 1.0, resume ? state->t : 1.0,
+                              resume ? state->k : 0, tol, st);
+    sc.done(2, 0.0, 2.0 * bytes);
+  }
   lt::PgaFuse f;
   f.mask = mask;
   f.obs = obs;
@@ -484,6 +564,14 @@ lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8_t* mas
   io.scal = scal;
   io.scratch = w + L.jac;
   io.info = info;
+  // algorithmic traffic of the fused transforms: forward reads X, X_old, obs, mask and
+  // writes G_hat; inverse reads D_hat, X, X_old (+ mask, obs for the objective) and
+  // writes X_new; intermediate passes read and write the tensor once more each
+  const double eb = (double)c.elem;
+  const double fwd_bytes = Nd * (4 * eb + 1) + (L.fwd.npass - 1) * 2 * Nd * eb;
+  const double inv_bytes = Nd * (4 * eb + (c.objective ? eb + 1 : 0)) + (L.inv.npass - 1) * 2 * Nd * eb;
+  const double fwd_flops = transform_flops(L.fwd, I1 * I2, c.P) + 6 * Nd;
+  const double inv_flops = transform_flops(L.inv, I1 * I2, c.P) + 7 * Nd;
   for (int64_t j = 0; j < iters && e == cudaSuccess; ++j) {
     void* cur = (j % 2 == 0) ? X : X2;
     void* old = (j % 2 == 0) ? X2 : X;
@@ -491,16 +579,29 @@ lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8_t* mas
     f.x_old = old;
     f.x_out = old;
     int rows = 0;
-    e = lt::launch_transform(c, L.fwd, nullptr, Gh, lt::FUSE_PGA_FORWARD, &f, st, nullptr);
-    if (e == cudaSuccess) e = lt::launch_jacobi(c, L.jp, io, st);
-    if (e == cudaSuccess)
+    {
+      Scope sc(c, st, LT_K_TRANSFORM);
+      e = lt::launch_transform(c, L.fwd, nullptr, Gh, lt::FUSE_PGA_FORWARD, &f, st, nullptr);
+      sc.done(L.fwd.npass, fwd_flops, fwd_bytes);
+    }
+    if (e == cudaSuccess) e = run_jacobi(c, L.jp, io, st);
+    if (e == cudaSuccess) {
+      Scope sc(c, st, LT_K_TRANSFORM);
       e = lt::launch_transform(c, L.inv, Gh, Gh, lt::FUSE_PGA_INVERSE, &f, st, &rows);
-    if (e == cudaSuccess)
+      sc.done(L.inv.npass, inv_flops, inv_bytes);
+    }
+    if (e == cudaSuccess) {
+      Scope sc(c, st, LT_K_AUX);
       e = lt::launch_pga_finish(scal, partials, rows, info, c.P, tau, c.objective,
                                 c.d_status, st);
+      sc.done(1, 0.0, 0.0);
+    }
   }
-  if (e == cudaSuccess)
+  if (e == cudaSuccess) {
+    Scope sc(c, st, LT_K_AUX);
     e = lt::launch_select_result(scal, X, X2, state ? state->X_prev : nullptr, bytes, st);
+    sc.done(1, 0.0, 3.0 * bytes);
+  }
   if (e == cudaSuccess && (report || state)) {
     e = cudaMemcpyAsync(c.h_pinned, scal, sizeof(lt::PgaScalars), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) {
@@ -551,6 +652,27 @@ lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const int64_t* 
     off += align256(b);
   }
   return LT_OK;
+}
+
+lt_status lt_ctx_get_stats(lt_ctx ctx, lt_stats* out, int reset) {
+  if (!ctx || !out) return LT_ERR_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  cudaError_t e = cudaDeviceSynchronize();
+  for (auto& r : c->pending) {
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    c->stats.k[r.fam].ms += ms;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->pending.clear();
+  double dev[4] = {0, 0, 0, 0};
+  if (e == cudaSuccess) e = cudaMemcpy(dev, c->d_counters, sizeof(dev), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, sizeof(dev));
+  for (int i = 0; i < 4; ++i) c->stats.k[i].flops += dev[i];
+  *out = c->stats;
+  if (reset) c->stats = lt_stats{};
+  return cuda_status(e);
 }
 
 lt_status lt_last_device_status(lt_ctx ctx, int32_t* out) {

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "lt.h"
 
 namespace lt {
@@ -35,6 +37,13 @@ struct Ctx {
   int objective = 0;
   // Pinned host staging for asynchronous reports
   void* h_pinned = nullptr;
+  // Statistics (lt_ctx_get_stats)
+  int profile = 0;
+  lt_stats stats = {};
+  double* d_counters = nullptr;       // device: [LT_K_JACOBI] executed Jacobi flops
+  struct EventRec { cudaEvent_t a, b; int fam; };
+  std::vector<EventRec> pending;
+  std::vector<cudaEvent_t> pool;
 };
 
 // ----------------------------------------------------------------------------------
@@ -140,6 +149,7 @@ struct JacobiIO {
   const PgaScalars* scal = nullptr;  // PGA: skip when done
   void* scratch = nullptr;  // jp.ws_bytes
   SliceInfo* info = nullptr;
+  double* flops = nullptr;  // device counter of executed flops (atomic, per slice)
 };
 
 cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io,

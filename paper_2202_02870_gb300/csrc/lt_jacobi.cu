@@ -118,7 +118,7 @@ jacobi_kernel(const JArgs a) {
   int* list = reinterpret_cast<int*>(sp); sp += sizeof(int) * np;        // SVT: kept columns / SVD: rank
   T* coef = reinterpret_cast<T*>(sp); sp += sizeof(T) * (size_t)kWarps * np;  // per-warp coefficients
   T* vtmp = reinterpret_cast<T*>(sp); sp += sizeof(T) * (size_t)(jp.mode == JAC_SVD ? 2 * m : 0);
-  __shared__ int s_count, s_cand;
+  __shared__ int s_count, s_cand, s_rot;
   __shared__ T s_red[kWarps];
 
   const T* Ain = reinterpret_cast<const T*>(a.io.A);
@@ -157,6 +157,8 @@ jacobi_kernel(const JArgs a) {
 
     // ---- sweeps
     int sweeps = 0;
+    int nrot = 0;  // rotations applied by this warp (flop accounting)
+    if (threadIdx.x == 0) s_rot = 0;
     bool rotated = true;
     while (rotated && sweeps < a.max_sweeps) {
       for (int c = warp; c < np; c += kWarps) {
@@ -188,13 +190,17 @@ jacobi_kernel(const JArgs a) {
           if (al > T(0) && be > T(0) && g * g > tol2 * al * be) {
             T cs, sn, t;
             rotation(al, be, g, cs, sn, t);
+            // x' = c x - s y = x - s (y + h x),  y' = s x + c y = y + s (x - h y) with
+            // h = s / (1 + c) = tan(theta/2): the update is formed as a small increment,
+            // so a small rotation adds rounding error of the order of the increment.
+            const T h = sn / (T(1) + cs);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
               const int r = lane + 32 * e;
               const T xi = x[e], yi = y[e];
               if (r < m) {
-                ci[r] = cs * xi - sn * yi;
-                cj[r] = sn * xi + cs * yi;
+                ci[r] = fma(-sn, fma(h, xi, yi), xi);
+                cj[r] = fma(sn, fma(-h, yi, xi), yi);
               }
             }
             if (jp.mode == JAC_SVD) {
@@ -202,8 +208,8 @@ jacobi_kernel(const JArgs a) {
               T* vj = Vj + (size_t)np * j;
               for (int r = lane; r < np; r += 32) {
                 const T xi = vi[r], yi = vj[r];
-                vi[r] = cs * xi - sn * yi;
-                vj[r] = sn * xi + cs * yi;
+                vi[r] = fma(-sn, fma(h, xi, yi), xi);
+                vj[r] = fma(sn, fma(-h, yi, xi), yi);
               }
             }
             if (lane == 0) {
@@ -211,6 +217,7 @@ jacobi_kernel(const JArgs a) {
               nrm[j] = be + t * g;
             }
             flag = 1;
+            ++nrot;
           }
         }
         __syncthreads();
@@ -226,6 +233,8 @@ jacobi_kernel(const JArgs a) {
       acc = warp_allsum(acc);
       if (lane == 0) nrm[c] = acc;
     }
+    __syncthreads();
+    if (lane == 0 && nrot) atomicAdd(&s_rot, nrot);
     __syncthreads();
     if (threadIdx.x == 0) {
       int st = 0;
@@ -250,6 +259,13 @@ jacobi_kernel(const JArgs a) {
           }
         }
         s_count = k;
+        if (a.io.flops) {
+          // pairs visited (dot) + rotations + norm passes + reconstruction 4kmn
+          const double md = m, nd = n;
+          const double f = sweeps * (nd * (nd - 1) * md + 2 * md * nd) + 6.0 * md * s_rot +
+                           2 * md * nd + 4.0 * k * md * nd;
+          atomicAdd(a.io.flops, f);
+        }
         if (a.io.info) {
           a.io.info[slice].rank = k;
           a.io.info[slice].nuclear = double(nuc);
@@ -311,6 +327,11 @@ jacobi_kernel(const JArgs a) {
     } else {
       // ---- SVD: sort descending, write Sigma, the Jacobi V side and the W side
       const int64_t I2 = jp.I2;
+      if (threadIdx.x == 0 && a.io.flops) {
+        const double md = m, nd = n;
+        atomicAdd(a.io.flops, sweeps * (nd * (nd - 1) * md + 2 * md * nd) +
+                                  (6.0 * md + 6.0 * np) * s_rot + 2 * md * nd);
+      }
       T sig_max = T(0);
       for (int c = 0; c < n; ++c) sig_max = fmax(sig_max, sqrt(nrm[c]));
       for (int c = threadIdx.x; c < n; c += blockDim.x) {
@@ -505,7 +526,7 @@ cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io
   a.max_sweeps = c.max_sweeps;
   const double u = c.elem == 8 ? DBL_EPSILON / 2 : FLT_EPSILON / 2;
   a.tol = c.jacobi_tol > 0 ? c.jacobi_tol
-                           : (c.elem == 8 ? jp.m * u : 4.0 * std::sqrt((double)jp.m) * u);
+                           : (c.elem == 8 ? jp.m * u : std::sqrt((double)jp.m) * u);
   a.status = c.d_status;
   const int grid = jacobi_grid(c, jp);
   return c.elem == 8 ? launch_t<double>(a, grid, st) : launch_t<float>(a, grid, st);

@@ -25,7 +25,9 @@ STATUS = {0: "LT_OK", -1: "LT_ERR_ARG", -2: "LT_ERR_SHAPE", -3: "LT_ERR_SINGULAR
 LT_DEV_NOCONV, LT_DEV_NONFINITE, LT_DEV_TIMEOUT = 1, 2, 4
 LT_FP64, LT_FP32, LT_MIXED = 0, 1, 2
 LT_OP_TRANSFORM, LT_OP_INVERSE, LT_OP_PRODUCT, LT_OP_SVD, LT_OP_SVT, LT_OP_PGA = range(6)
-LT_OPT_MAX_SWEEPS, LT_OPT_JACOBI_TOL, LT_OPT_OBJECTIVE = 0, 1, 2
+LT_OPT_MAX_SWEEPS, LT_OPT_JACOBI_TOL, LT_OPT_OBJECTIVE, LT_OPT_PROFILE = 0, 1, 2, 3
+LT_K_TRANSFORM, LT_K_JACOBI, LT_K_GEMM, LT_K_AUX = 0, 1, 2, 3
+KERNEL_FAMILIES = ("transform", "jacobi", "gemm", "aux")
 
 # Every entry point of include/lt.h: name -> (restype, argtypes)
 _vp, _i64, _dbl, _sz = C.c_void_p, C.c_int64, C.c_double, C.c_size_t
@@ -40,6 +42,15 @@ class lt_pga_report(C.Structure):
     _fields_ = [("iters_done", C.c_int64), ("rel_residual", C.c_double),
                 ("objective", C.c_double), ("max_sweeps_used", C.c_int32),
                 ("device_status", C.c_int32)]
+
+
+class lt_kernel_stats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("ms", C.c_double), ("flops", C.c_double),
+                ("bytes", C.c_double)]
+
+
+class lt_stats(C.Structure):
+    _fields_ = [("k", lt_kernel_stats * 4)]
 
 
 SIGNATURES = {
@@ -65,6 +76,7 @@ SIGNATURES = {
                                           C.POINTER(C.c_void_p), C.POINTER(C.c_double),
                                           C.POINTER(C.c_double), _i64, C.POINTER(C.c_void_p),
                                           C.POINTER(lt_pga_report), _vp, _sz, _vp]),
+    "lt_ctx_get_stats": (C.c_int, [_vp, C.POINTER(lt_stats), C.c_int]),
     "lt_last_device_status": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "lt_status_string": (C.c_char_p, [C.c_int]),
 }
@@ -294,6 +306,16 @@ def lt_pga_complete_batched(ctxs, masks, obss, taus, steps, iters, Xs, reports=N
     if reports is not None:
         reports.append(rep_arr)
     return Xs
+
+
+def lt_ctx_get_stats(ctx, reset: bool = False) -> dict:
+    """Per kernel family: launches, summed event ms (LT_OPT_PROFILE), algorithmic flops
+    and bytes."""
+    st = lt_stats()
+    _check("lt_ctx_get_stats", lib().lt_ctx_get_stats(ctx.handle, C.byref(st), int(bool(reset))))
+    return {name: {"launches": int(st.k[i].launches), "ms": float(st.k[i].ms),
+                   "flops": float(st.k[i].flops), "bytes": float(st.k[i].bytes)}
+            for i, name in enumerate(KERNEL_FAMILIES)}
 
 
 def lt_last_device_status(ctx) -> int:
