@@ -271,7 +271,7 @@ def run_ours(args):
         peaks = load_peaks()
         line = {
             "metric": METRIC,
-            "value": round(value, 3),
+            "value": round(value, 5),
             "unit": "iters/s",
             "n_gpus": ws,
             "steps": args.steps,
@@ -307,7 +307,8 @@ def run_ours(args):
                 "unit": "GFLOP/s", "peak": FP64_PEAK_GFLOPS,
                 "hbm_gbs": round(tra["bytes"] / max(tra["ms"], 1e-9) / 1e6, 1),
                 "hbm_peak_gbs": peaks.get("hbm_gbs")},
-            "e2e": {"value": round(ws * iters / (e2e_step / 1e3), 3), "unit": "iters/s",
+            "e2e": {"value": round(ws * iters / (e2e_step / 1e3), 5), "unit": "iters/s",
+                    "ms_per_step": round(e2e_step, 3),
                     "h2d_bytes_per_step": int(N + N * 8), "d2h_bytes_per_step": int(N * 8)},
             "gpu_launches": int(gpu_launches),
             "clocks": clocks,
@@ -318,6 +319,47 @@ def run_ours(args):
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_case(args):
+    """Auxiliary single-operation runs used for profiling (not the benchmark line):
+    --case svt     lt_svt (tau 0.5) of the 144x176x3x32 tensor G = P_Omega(M) of the
+                   completion problem (what the first PGA iteration thresholds);
+    --case product lt_product U *_L V^T of its 144x10x3x32 and 10x176x3x32 factors."""
+    import torch
+    from paper_2202_02870_gb300 import lt
+    prec = lt.LT_FP64 if args.precision == "fp64" else lt.LT_FP32
+    dt = torch.float64 if prec == lt.LT_FP64 else torch.float32
+    c = problem_inputs(0)
+    dev = torch.device("cuda", 0)
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.ravel(order="F"))).to(dt).reshape(
+        tuple(reversed(a.shape))).to(dev)
+    ctx = lt.Context([3, 32], [lt.lt_make_dct(3), lt.lt_make_dct(32)], prec)
+    if args.case == "svt":
+        G = to_dev(c["mask"] * np.random.default_rng(1).standard_normal(c["mask"].shape))
+        D = torch.empty_like(G)
+        wsb = torch.empty(max(lt.lt_workspace_size(ctx, lt.LT_OP_SVT, 144, 176), 1),
+                          dtype=torch.uint8, device=dev)
+        run = lambda: lt.lt_svt(ctx, G, 0.5, D, ws=wsb)
+        units, unit = 96, "slices"
+    else:
+        U = to_dev(c["U"])
+        Vt = to_dev(np.asfortranarray(np.swapaxes(c["V"], 0, 1)))
+        X = torch.empty((32, 3, 176, 144), dtype=dt, device=dev)
+        run = lambda: lt.lt_product(ctx, U, Vt, X)
+        units, unit = 1, "products"
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"case": args.case, "precision": args.precision, "ms_per_call": ms,
+                      f"{unit}_per_s": units / (ms / 1e3)}))
 
 
 def run_reference(args):
@@ -360,12 +402,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=15)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--case", default="pga", choices=["pga", "svt", "product"],
+                    help="pga: the benchmark line; svt/product: single-operation runs "
+                         "used for profiling")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     from paper_2202_02870_gb300 import build
     build.build()
+    if args.case != "pga":
+        run_case(args)
+        return
     run_ours(args)
 
 
