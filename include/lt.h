@@ -233,6 +233,29 @@ LT_API lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const in
                                   lt_pga_report* reports, void* ws, size_t ws_bytes,
                                   void* stream);
 
+/* *_L-product without allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- e.g. an application that
+ * reserves all GPU memory for its own pool and forbids further cudaMalloc calls, or code
+ * that must not call cudaMalloc/cudaFree because they may synchronise the device --
+ * and so cannot pass lt_product a workspace.  It computes exactly what lt_product
+ * computes (same kernels; same arguments minus the workspace) with the transform-domain
+ * operands L(A) and L(B) placed in a fixed array inside the library's device memory,
+ * LT_NOALLOC_SCRATCH_BYTES (32 MiB) large, which every GPU that loads the library's
+ * module holds until the process exits.
+ * Limits: align256(I1*l*P*elem) + align256(l*I2*P*elem) must not exceed
+ *   LT_NOALLOC_SCRATCH_BYTES (align256 rounds up to a multiple of 256), else
+ *   LT_ERR_SHAPE and nothing is enqueued.
+ * Set-up: the first call made while a device is current looks up the array's device
+ *   address on that device (cudaGetSymbolAddress); make that first call before any
+ *   stream capture.
+ * Sharing: all calls use the same array and it keeps the last call's contents (nothing
+ *   in it needs to start at zero).  Calls whose work overlaps on the GPU race on it:
+ *   order them, e.g. issue them on one stream.
+ * It calls no cudaMalloc, cudaFree or other allocating routine. */
+#define LT_NOALLOC_SCRATCH_BYTES (32u << 20)
+LT_API lt_status lt_product_noalloc(lt_ctx ctx, int64_t I1, int64_t l, int64_t I2,
+                                    const void* A, const void* B, void* C, void* stream);
+
 /* Counters of the context since creation or the last reset (reset != 0 clears them
  * after reading).  Synchronises the device when LT_OPT_PROFILE is on or when Jacobi
  * flops are pending.  out: host. */

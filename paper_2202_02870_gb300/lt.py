@@ -76,6 +76,7 @@ SIGNATURES = {
                                           C.POINTER(C.c_void_p), C.POINTER(C.c_double),
                                           C.POINTER(C.c_double), _i64, C.POINTER(C.c_void_p),
                                           C.POINTER(lt_pga_report), _vp, _sz, _vp]),
+    "lt_product_noalloc": (C.c_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp]),
     "lt_ctx_get_stats": (C.c_int, [_vp, C.POINTER(lt_stats), C.c_int]),
     "lt_last_device_status": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "lt_status_string": (C.c_char_p, [C.c_int]),
@@ -238,6 +239,23 @@ def lt_product(ctx, A, B, Cout, ws=None, stream=None):
     ws, nb = _workspace(ctx, need, A.device, ws)
     _check("lt_product", lib().lt_product(ctx.handle, I1, l, I2, _ptr(A), _ptr(B), _ptr(Cout),
                                           _ptr(ws), nb, _stream(stream)))
+    return Cout
+
+
+LT_NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def lt_product_noalloc(ctx, A, B, Cout, stream=None):
+    """lt_product for callers that cannot allocate: no workspace argument; the library
+    uses its fixed LT_NOALLOC_SCRATCH_BYTES device array (see include/lt.h)."""
+    for t, n in ((A, "A"), (B, "B"), (Cout, "C")):
+        _require(t, ctx, n)
+    I1, l = _dims(A)
+    l2, I2 = _dims(B)
+    if l2 != l:
+        raise ValueError("inner sizes of A and B differ")
+    _check("lt_product_noalloc", lib().lt_product_noalloc(ctx.handle, I1, l, I2, _ptr(A), _ptr(B),
+                                                          _ptr(Cout), _stream(stream)))
     return Cout
 
 
