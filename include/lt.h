@@ -82,8 +82,11 @@ typedef enum {
 typedef enum {
   LT_OPT_MAX_SWEEPS = 0,     /* Jacobi sweep limit (default 40); NOCONV when hit */
   LT_OPT_JACOBI_TOL = 1,     /* pair tolerance: rotate when |a.b| > tol*sqrt(a.a b.b);
-                                value <= 0 restores the default (m * unit roundoff for
-                                LT_FP64, sqrt(m) * unit roundoff otherwise) */
+                                value <= 0 restores the default: r * unit roundoff for
+                                LT_FP64, sqrt(r) * unit roundoff otherwise, r = rows of
+                                the matrix being orthogonalised (min(I1,I2) for the SVT,
+                                which works on the triangular factor of a pivoted QR;
+                                max(I1,I2) for the SVD) */
   LT_OPT_OBJECTIVE = 2,      /* PGA: also accumulate the objective (0/1, default 0) */
   LT_OPT_PROFILE = 3         /* 1: bracket every kernel launch with CUDA events on its
                                 stream, summed per kernel family by lt_ctx_get_stats */

@@ -125,6 +125,7 @@ struct JacobiPlan {
   bool transposed = false;              // working matrix is A^T (I1 < I2)
   bool w_in_smem = true;
   int E = 1;                            // elements per lane per column chunk
+  int G = 32;                           // lanes per column pair (SVT kernel)
   int threads = 512;
   int smem = 0;
   size_t ws_bytes = 0;                  // scratch bytes (global W, Jacobi V, info)

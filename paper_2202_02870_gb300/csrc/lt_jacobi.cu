@@ -1,50 +1,29 @@
-// Kernel J: per-slice SVD in the transform domain (Algorithm 3, line "svd(A_hat^i)")
-// and the singular value thresholding of Algorithm 4 (shrink max(sigma - tau, 0) and
-// reconstruct U S V^T), one CTA per frontal slice.
+// Kernel J, SVD form (Algorithm 3: svd of every slice A_hat^p, full U, S, V), plus the
+// planning and dispatch of both Jacobi kernels.  The SVT form used by lt_svt and PGA
+// (Algorithm 4) is in lt_jacobi_svt.cuh.
 //
 // Method: one-sided (Hestenes) Jacobi on the working matrix B (m x n, m >= n): B = A^p
-// when I1 >= I2, B = (A^p)^T otherwise, so that the n <= m columns are orthogonalised.
-// Plane rotations are applied from the right, B <- B J, until every pair of columns is
-// orthogonal to the tolerance: |b_i . b_j| <= tol * ||b_i|| ||b_j||.  At convergence
-// B = W = U Sigma (columns of norm sigma_i) and the accumulated rotations are V.
-// Rotation parameters follow Rutishauser's formulas (Golub & Van Loan, Matrix
-// Computations, 4th ed., Sec. 8.6.3): zeta = (beta - alpha)/(2 gamma),
-// t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)), c = 1/sqrt(1 + t^2), s = c t, with
-// alpha = ||b_i||^2, beta = ||b_j||^2, gamma = b_i . b_j; the squared norms are updated
-// as alpha - t gamma, beta + t gamma and recomputed exactly at the start of each sweep.
-//
-// Parallel ordering: round-robin ("circle") tournament over the n (padded to even)
-// columns: n - 1 rounds of n/2 disjoint pairs per sweep; a warp owns one pair at a time
-// and keeps both columns in registers (lane l holds rows l, l+32, ...), so a pair costs
-// one read and one write of its two columns plus a warp-shuffle reduction of b_i . b_j.
-//
-// SVT reconstruction without V: with W = B V (orthogonal columns w_i, ||w_i|| = sigma_i)
-// the shrunk slice is D_B = W diag((sigma - tau)_+ / sigma) V^T, and since
-// V^T = Sigma^{-2} W^T B, D_B = sum_{sigma_i > tau} g_i w_i (w_i^T B) with
-// g_i = (sigma_i - tau) / sigma_i^3: every column b_j of the ORIGINAL slice is mapped
-// to D_B b_j by k dot products and k axpys (k = number of sigma_i > tau).  V is never
-// formed, so the rotations only touch B.
+// when I1 >= I2, B = (A^p)^T otherwise.  Plane rotations are applied from the right,
+// B <- B J, until every pair of columns is orthogonal to the tolerance
+// |b_i . b_j| <= tol ||b_i|| ||b_j||.  At convergence B = W = U Sigma and the accumulated
+// rotations (kept in global scratch) are V.  Round-robin ordering, a warp per pair with
+// both columns in registers; squared norms updated as alpha - t gamma, beta + t gamma and
+// recomputed exactly at the start of each sweep.  The outputs are sorted by descending
+// sigma and the W side is completed to a square orthogonal basis.
 #include <algorithm>
 #include <cfloat>
 
-#include "lt_internal.cuh"
+#include "lt_jacobi_common.cuh"
 
 namespace lt {
 namespace {
 
-constexpr int kJThreads = 512;
-constexpr int kWarps = kJThreads / 32;
-
-template <typename T>
-__device__ __forceinline__ T warp_allsum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <typename T> __device__ __forceinline__ T unit_roundoff();
-template <> __device__ __forceinline__ double unit_roundoff<double>() { return DBL_EPSILON / 2; }
-template <> __device__ __forceinline__ float unit_roundoff<float>() { return FLT_EPSILON / 2; }
+using jac::JArgs;
+using jac::kJThreads;
+using jac::kWarps;
+using jac::rotation;
+using jac::unit_roundoff;
+using jac::warp_allsum;
 
 // Round-robin pairing: column n-1 is fixed, the others rotate on a circle.
 __device__ __forceinline__ void rr_pair(int r, int k, int n, int& i, int& j) {
@@ -57,46 +36,6 @@ __device__ __forceinline__ void rr_pair(int r, int k, int n, int& i, int& j) {
     j = (r - k + c) % c;
   }
 }
-
-// Rotation for the pair (alpha, beta, gamma).  The angle only steers convergence; what
-// must hold to working precision is c^2 + s^2 = 1, so that B J stays an orthogonal
-// transform of B.  FP32: Rutishauser's formulas directly.  FP64: the tangent t is
-// taken from the same formulas in FP32 (FP64 divides and square roots cost tens of
-// FP64 pipe slots each on this GPU), then c = (1 + t^2)^{-1/2} is computed in FP64 by
-// two Newton steps y <- y (3 - x y^2) / 2 from the FP32 reciprocal square root
-// (2^-22 -> 2^-44 -> full precision), s = c t.  A tangent that is only FP32-accurate
-// leaves |b_i . b_j| at ~1e-7 of its value after the rotation; later sweeps remove it.
-__device__ __forceinline__ void rotation(float al, float be, float g, float& cs, float& sn,
-                                         float& t) {
-  const float zeta = (be - al) / (2.f * g);
-  const float az = fabsf(zeta);
-  t = (az > 1e15f) ? 0.5f / az : 1.f / (az + sqrtf(1.f + az * az));
-  if (zeta < 0.f) t = -t;
-  cs = rsqrtf(1.f + t * t);
-  sn = cs * t;
-}
-__device__ __forceinline__ void rotation(double al, double be, double g, double& cs,
-                                         double& sn, double& t) {
-  const float zeta = float(be - al) / (2.f * float(g));
-  const float az = fabsf(zeta);
-  float tf = (az > 1e15f) ? 0.5f / az : 1.f / (az + sqrtf(1.f + az * az));
-  if (zeta < 0.f) tf = -tf;
-  t = double(tf);
-  const double x = fma(t, t, 1.0);
-  double y = double(rsqrtf(float(x)));
-  y = y * fma(-0.5 * x, y * y, 1.5);
-  y = y * fma(-0.5 * x, y * y, 1.5);
-  cs = y;
-  sn = y * t;
-}
-
-struct JArgs {
-  JacobiPlan jp;
-  JacobiIO io;
-  double tol;
-  int max_sweeps;
-  int32_t* status;
-};
 
 template <typename T, int E>
 __global__ void __launch_bounds__(kJThreads)
@@ -482,6 +421,41 @@ int jacobi_grid(const Ctx& c, const JacobiPlan& jp) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(jp.P, (int64_t)c.sms * 2));
 }
 
+// Group width G (lanes per column pair) and rows per lane E of the SVT kernel, from the
+// instantiated set (rows padded to G E >= n).  Returns false when n is too large.
+bool svt_shape(int n, int elem, int* G, int* E) {
+  static const int kE8[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 18, 20, 24};
+  static const int kEhi[] = {14, 16, 18, 20, 24, 28, 32};
+  static const int kE16d[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12};
+  static const int kE32d[] = {8, 10, 12, 14, 16};
+  auto pick = [](const int* set, int cnt, int need) {
+    for (int i = 0; i < cnt; ++i)
+      if (set[i] >= need) return set[i];
+    return -1;
+  };
+  int g, e = -1;
+  if (elem == 4) {
+    if (n <= 192) { g = 8; e = pick(kE8, 15, (n + 7) / 8); }
+    else if (n <= 384) { g = 16; e = pick(kEhi, 5, (n + 15) / 16); }
+    else { g = 32; e = pick(kEhi, 7, (n + 31) / 32); }
+  } else {
+    if (n <= 192) { g = 16; e = pick(kE16d, 11, (n + 15) / 16); }
+    else { g = 32; e = pick(kE32d, 5, (n + 31) / 32); }
+  }
+  if (e < 0) return false;
+  *G = g;
+  *E = e;
+  return true;
+}
+
+template <typename T>
+size_t svt_smem(const JacobiPlan& jp) {
+  size_t b = 0;
+  if (jp.w_in_smem) b += sizeof(T) * (size_t)jp.ld * jp.npad;
+  b += sizeof(T) * 2 * (size_t)jp.npad + sizeof(int) * 2 * (size_t)jp.npad;
+  return (b + 15) & ~size_t(15);
+}
+
 }  // namespace
 
 lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan* out) {
@@ -494,19 +468,41 @@ lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan
   jp.m = (int)std::max(I1, I2);
   jp.n = (int)std::min(I1, I2);
   jp.npad = jp.n + (jp.n & 1);
-  jp.ld = jp.m | 1;  // odd leading dimension: conflict-free transposed stores
-  const int maxE = c.elem == 8 ? 16 : 32;
-  int E = 1;
-  while (32 * E < jp.m) E *= 2;
-  if (E > maxE) return LT_ERR_SHAPE;  // column must fit the registers of a warp
-  jp.E = E;
   jp.threads = kJThreads;
   jp.w_in_smem = true;
-  size_t need = c.elem == 8 ? smem_need<double>(jp) : smem_need<float>(jp);
-  if (need > (size_t)kSmemOptin - 1024) {
-    jp.w_in_smem = false;
+  size_t need;
+  if (mode == JAC_SVT) {
+    // QR-preconditioned kernel: Jacobi on the n x n factor R^T, G lanes per column
+    // pair holding E rows each, leading dimension >= max(m, G E) and odd (conflict-free
+    // transposed stores); as many warps as the pairs of a round need, within the cap.
+    int G = 0, E = 0;
+    if (!svt_shape(jp.n, c.elem, &G, &E)) return LT_ERR_SHAPE;
+    jp.G = G;
+    jp.E = E;
+    jp.ld = std::max(jp.m, G * E) | 1;
+    const int ppw = 32 / G;
+    const int maxw = (c.elem == 8 ? jac::kMaxThreadsF64 : jac::kMaxThreadsF32) / 32;
+    const int want = (jp.npad / 2 + ppw - 1) / ppw;
+    jp.threads = 32 * std::max(4, std::min(maxw, want));
+    need = c.elem == 8 ? svt_smem<double>(jp) : svt_smem<float>(jp);
+    if (need > (size_t)kSmemOptin - 1024) {
+      jp.w_in_smem = false;
+      need = c.elem == 8 ? svt_smem<double>(jp) : svt_smem<float>(jp);
+      if (need > (size_t)kSmemOptin - 1024) return LT_ERR_SHAPE;
+    }
+  } else {
+    jp.ld = jp.m | 1;  // odd leading dimension: conflict-free transposed stores
+    const int maxE = c.elem == 8 ? 16 : 32;
+    int E = 1;
+    while (32 * E < jp.m) E *= 2;
+    if (E > maxE) return LT_ERR_SHAPE;  // column must fit the registers of a warp
+    jp.E = E;
     need = c.elem == 8 ? smem_need<double>(jp) : smem_need<float>(jp);
-    if (need > (size_t)kSmemOptin - 1024) return LT_ERR_SHAPE;
+    if (need > (size_t)kSmemOptin - 1024) {
+      jp.w_in_smem = false;
+      need = c.elem == 8 ? smem_need<double>(jp) : smem_need<float>(jp);
+      if (need > (size_t)kSmemOptin - 1024) return LT_ERR_SHAPE;
+    }
   }
   jp.smem = (int)need;
   const int grid = jacobi_grid(c, jp);
@@ -524,11 +520,19 @@ cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io
   a.jp = jp;
   a.io = io;
   a.max_sweeps = c.max_sweeps;
+  // default pair tolerance: rows of the orthogonalised matrix (n for the SVT kernel,
+  // which works on R^T; m for the SVD kernel) times u in FP64, sqrt(rows) u in FP32
   const double u = c.elem == 8 ? DBL_EPSILON / 2 : FLT_EPSILON / 2;
-  a.tol = c.jacobi_tol > 0 ? c.jacobi_tol
-                           : (c.elem == 8 ? jp.m * u : std::sqrt((double)jp.m) * u);
+  const double rows = jp.mode == JAC_SVT ? jp.n : jp.m;
+  a.tol = c.jacobi_tol > 0 ? c.jacobi_tol : (c.elem == 8 ? rows * u : std::sqrt(rows) * u);
   a.status = c.d_status;
   const int grid = jacobi_grid(c, jp);
+  if (jp.mode == JAC_SVT) {
+    if (c.elem == 8) return jac::launch_svt_f64(a, grid, st);
+    if (jp.G == 8)
+      return jp.E <= 8 ? jac::launch_svt_f32_g8_small(a, grid, st) : jac::launch_svt_f32_g8_large(a, grid, st);
+    return jac::launch_svt_f32_g16_32(a, grid, st);
+  }
   return c.elem == 8 ? launch_t<double>(a, grid, st) : launch_t<float>(a, grid, st);
 }
 

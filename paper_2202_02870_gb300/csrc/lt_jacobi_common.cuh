@@ -1,0 +1,89 @@
+// Device helpers shared by the Jacobi kernels (kernel J).
+#pragma once
+
+#include <cfloat>
+
+#include "lt_internal.cuh"
+
+namespace lt {
+namespace jac {
+
+constexpr int kJThreads = 512;
+constexpr int kWarps = kJThreads / 32;
+
+template <typename T>
+__device__ __forceinline__ T warp_allsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// (value, index) arg-max over the warp; ties go to the smaller index.  Every lane ends
+// with the result.
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T& v, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) { v = ov; i = oi; }
+  }
+}
+
+template <typename T> __device__ __forceinline__ T unit_roundoff();
+template <> __device__ __forceinline__ double unit_roundoff<double>() { return DBL_EPSILON / 2; }
+template <> __device__ __forceinline__ float unit_roundoff<float>() { return FLT_EPSILON / 2; }
+
+// Rotation for the pair (alpha, beta, gamma) = (||x||^2, ||y||^2, x.y), Rutishauser's
+// formulas (Golub & Van Loan, Matrix Computations, 4th ed., Sec. 8.6.3):
+// zeta = (beta - alpha)/(2 gamma), t = sign(zeta)/(|zeta| + sqrt(1 + zeta^2)),
+// c = 1/sqrt(1 + t^2), s = c t.  The angle only steers convergence; what must hold to
+// working precision is c^2 + s^2 = 1, so that the update is an orthogonal transform.
+// FP32: the formulas directly.  FP64: the tangent is taken from the same formulas in
+// FP32 (FP64 divides and square roots cost tens of FP64 pipe slots each on this GPU),
+// then c = (1 + t^2)^{-1/2} is computed in FP64 by two Newton steps
+// y <- y (3 - x y^2) / 2 from the FP32 reciprocal square root (2^-22 -> 2^-44 -> full
+// precision), s = c t.  A tangent that is only FP32-accurate leaves |x.y| at ~1e-7 of
+// its value after the rotation; later sweeps remove it.
+__device__ __forceinline__ void rotation(float al, float be, float g, float& cs, float& sn,
+                                         float& t) {
+  const float zeta = (be - al) / (2.f * g);
+  const float az = fabsf(zeta);
+  t = (az > 1e15f) ? 0.5f / az : 1.f / (az + sqrtf(1.f + az * az));
+  if (zeta < 0.f) t = -t;
+  cs = rsqrtf(1.f + t * t);
+  sn = cs * t;
+}
+__device__ __forceinline__ void rotation(double al, double be, double g, double& cs,
+                                         double& sn, double& t) {
+  const float zeta = float(be - al) / (2.f * float(g));
+  const float az = fabsf(zeta);
+  float tf = (az > 1e15f) ? 0.5f / az : 1.f / (az + sqrtf(1.f + az * az));
+  if (zeta < 0.f) tf = -tf;
+  t = double(tf);
+  const double x = fma(t, t, 1.0);
+  double y = double(rsqrtf(float(x)));
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  cs = y;
+  sn = y * t;
+}
+
+struct JArgs {
+  JacobiPlan jp;
+  JacobiIO io;
+  double tol;
+  int max_sweeps;
+  int32_t* status;
+};
+
+// SVT kernel launchers by element type and group width (lt_jacobi_f32*.cu, _f64.cu).
+constexpr int kMaxThreadsF32 = 768;
+constexpr int kMaxThreadsF64 = 576;
+cudaError_t launch_svt_f32_g8_small(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f32_g8_large(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f32_g16_32(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f64(const JArgs& a, int grid, cudaStream_t st);
+
+}  // namespace jac
+}  // namespace lt
