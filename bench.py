@@ -335,6 +335,7 @@ def run_case(args):
     to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.ravel(order="F"))).to(dt).reshape(
         tuple(reversed(a.shape))).to(dev)
     ctx = lt.Context([3, 32], [lt.lt_make_dct(3), lt.lt_make_dct(32)], prec)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_GROUP, args.jacobi_group)
     if args.case == "svt":
         G = to_dev(c["mask"] * np.random.default_rng(1).standard_normal(c["mask"].shape))
         D = torch.empty_like(G)
@@ -358,7 +359,8 @@ def run_case(args):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"case": args.case, "precision": args.precision, "ms_per_call": ms,
+    print(json.dumps({"case": args.case, "precision": args.precision,
+                      "jacobi_group": args.jacobi_group, "ms_per_call": ms,
                       f"{unit}_per_s": units / (ms / 1e3)}))
 
 
@@ -406,6 +408,8 @@ def main():
                     help="pga: the benchmark line; svt/product: single-operation runs "
                          "used for profiling")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--jacobi-group", type=int, default=0, choices=[0, 8, 16, 32],
+                    help="lanes per Jacobi column pair (0: the planner's choice)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -88,8 +88,10 @@ typedef enum {
                                 which works on the triangular factor of a pivoted QR;
                                 max(I1,I2) for the SVD) */
   LT_OPT_OBJECTIVE = 2,      /* PGA: also accumulate the objective (0/1, default 0) */
-  LT_OPT_PROFILE = 3         /* 1: bracket every kernel launch with CUDA events on its
+  LT_OPT_PROFILE = 3,        /* 1: bracket every kernel launch with CUDA events on its
                                 stream, summed per kernel family by lt_ctx_get_stats */
+  LT_OPT_JACOBI_GROUP = 4    /* SVT kernel: lanes per column pair (8, 16 or 32); 0 (the
+                                default) lets the planner choose from min(I1, I2) */
 } lt_option;
 
 /* Kernel families counted by lt_ctx_get_stats. */

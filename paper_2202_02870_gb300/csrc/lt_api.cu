@@ -349,6 +349,10 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
     case LT_OPT_PROFILE:
       c->profile = value != 0.0;
       return LT_OK;
+    case LT_OPT_JACOBI_GROUP:
+      if (!(value == 0 || value == 8 || value == 16 || value == 32)) return LT_ERR_ARG;
+      c->jacobi_group = (int)value;
+      return LT_OK;
   }
   return LT_ERR_ARG;
 }

@@ -35,6 +35,7 @@ struct Ctx {
   int max_sweeps = 40;
   double jacobi_tol = 0.0;            // <= 0: default
   int objective = 0;
+  int jacobi_group = 0;               // 0: planner's choice
   // Pinned host staging for asynchronous reports
   void* h_pinned = nullptr;
   // Statistics (lt_ctx_get_stats)

@@ -423,25 +423,37 @@ int jacobi_grid(const Ctx& c, const JacobiPlan& jp) {
 
 // Group width G (lanes per column pair) and rows per lane E of the SVT kernel, from the
 // instantiated set (rows padded to G E >= n).  Returns false when n is too large.
-bool svt_shape(int n, int elem, int* G, int* E) {
-  static const int kE8[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 18, 20, 24};
-  static const int kEhi[] = {14, 16, 18, 20, 24, 28, 32};
-  static const int kE16d[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12};
-  static const int kE32d[] = {8, 10, 12, 14, 16};
+bool svt_shape(int n, int elem, int force_g, int* G, int* E) {
+  // instantiated (G, E) per element type; rows padded to G E >= n
+  static const int kF8[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 18, 20, 24};
+  static const int kF16[] = {14, 16, 18, 20, 24};
+  static const int kF32[] = {14, 16, 18, 20, 24, 28, 32};
+  static const int kD8[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 16, 18};
+  static const int kD16[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14};
+  static const int kD32[] = {8, 10, 12, 14, 16};
   auto pick = [](const int* set, int cnt, int need) {
     for (int i = 0; i < cnt; ++i)
       if (set[i] >= need) return set[i];
     return -1;
   };
-  int g, e = -1;
-  if (elem == 4) {
-    if (n <= 192) { g = 8; e = pick(kE8, 15, (n + 7) / 8); }
-    else if (n <= 384) { g = 16; e = pick(kEhi, 5, (n + 15) / 16); }
-    else { g = 32; e = pick(kEhi, 7, (n + 31) / 32); }
-  } else {
-    if (n <= 192) { g = 16; e = pick(kE16d, 11, (n + 15) / 16); }
-    else { g = 32; e = pick(kE32d, 5, (n + 31) / 32); }
-  }
+  auto try_g = [&](int g) {
+    const int need = (n + g - 1) / g;
+    if (elem == 4) {
+      if (g == 8) return pick(kF8, 15, need);
+      if (g == 16) return pick(kF16, 5, need);
+      return pick(kF32, 7, need);
+    }
+    if (g == 8) return pick(kD8, 14, need);
+    if (g == 16) return pick(kD16, 12, need);
+    return pick(kD32, 5, need);
+  };
+  int g;
+  if (force_g) g = force_g;
+  else if (elem == 4) g = n <= 192 ? 8 : (n <= 384 ? 16 : 32);
+  else g = n <= 144 ? 8 : (n <= 224 ? 16 : 32);
+  int e = try_g(g);
+  if (e < 0 && force_g) return false;
+  while (e < 0 && g < 32) { g *= 2; e = try_g(g); }
   if (e < 0) return false;
   *G = g;
   *E = e;
@@ -476,10 +488,10 @@ lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan
     // pair holding E rows each, leading dimension >= max(m, G E) and odd (conflict-free
     // transposed stores); as many warps as the pairs of a round need, within the cap.
     int G = 0, E = 0;
-    if (!svt_shape(jp.n, c.elem, &G, &E)) return LT_ERR_SHAPE;
+    if (!svt_shape(jp.n, c.elem, c.jacobi_group, &G, &E)) return LT_ERR_SHAPE;
     jp.G = G;
     jp.E = E;
-    jp.ld = std::max(jp.m, G * E) | 1;
+    jp.ld = std::max(jp.m, 32 * ((G * E + 31) / 32)) | 1;
     const int ppw = 32 / G;
     const int maxw = (c.elem == 8 ? jac::kMaxThreadsF64 : jac::kMaxThreadsF32) / 32;
     const int want = (jp.npad / 2 + ppw - 1) / ppw;
@@ -528,7 +540,8 @@ cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io
   a.status = c.d_status;
   const int grid = jacobi_grid(c, jp);
   if (jp.mode == JAC_SVT) {
-    if (c.elem == 8) return jac::launch_svt_f64(a, grid, st);
+    if (c.elem == 8)
+      return jp.G == 8 ? jac::launch_svt_f64_g8(a, grid, st) : jac::launch_svt_f64_g16_32(a, grid, st);
     if (jp.G == 8)
       return jp.E <= 8 ? jac::launch_svt_f32_g8_small(a, grid, st) : jac::launch_svt_f32_g8_large(a, grid, st);
     return jac::launch_svt_f32_g16_32(a, grid, st);

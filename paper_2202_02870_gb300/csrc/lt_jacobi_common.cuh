@@ -83,7 +83,8 @@ constexpr int kMaxThreadsF64 = 576;
 cudaError_t launch_svt_f32_g8_small(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_g8_large(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_g16_32(const JArgs& a, int grid, cudaStream_t st);
-cudaError_t launch_svt_f64(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f64_g8(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f64_g16_32(const JArgs& a, int grid, cudaStream_t st);
 
 }  // namespace jac
 }  // namespace lt

@@ -14,25 +14,23 @@ static cudaError_t go(const JArgs& a, int grid, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_svt_f64(const JArgs& a, int grid, cudaStream_t st) {
+cudaError_t launch_svt_f64_g8(const JArgs& a, int grid, cudaStream_t st) {
   const int key = a.jp.G * 1000 + a.jp.E;
   switch (key) {
-    case 16001: return go<16, 1>(a, grid, st);
-    case 16002: return go<16, 2>(a, grid, st);
-    case 16003: return go<16, 3>(a, grid, st);
-    case 16004: return go<16, 4>(a, grid, st);
-    case 16005: return go<16, 5>(a, grid, st);
-    case 16006: return go<16, 6>(a, grid, st);
-    case 16007: return go<16, 7>(a, grid, st);
-    case 16008: return go<16, 8>(a, grid, st);
-    case 16009: return go<16, 9>(a, grid, st);
-    case 16010: return go<16, 10>(a, grid, st);
-    case 16012: return go<16, 12>(a, grid, st);
-    case 32008: return go<32, 8>(a, grid, st);
-    case 32010: return go<32, 10>(a, grid, st);
-    case 32012: return go<32, 12>(a, grid, st);
-    case 32014: return go<32, 14>(a, grid, st);
-    case 32016: return go<32, 16>(a, grid, st);
+    case 8001: return go<8, 1>(a, grid, st);
+    case 8002: return go<8, 2>(a, grid, st);
+    case 8003: return go<8, 3>(a, grid, st);
+    case 8004: return go<8, 4>(a, grid, st);
+    case 8005: return go<8, 5>(a, grid, st);
+    case 8006: return go<8, 6>(a, grid, st);
+    case 8007: return go<8, 7>(a, grid, st);
+    case 8008: return go<8, 8>(a, grid, st);
+    case 8009: return go<8, 9>(a, grid, st);
+    case 8010: return go<8, 10>(a, grid, st);
+    case 8012: return go<8, 12>(a, grid, st);
+    case 8014: return go<8, 14>(a, grid, st);
+    case 8016: return go<8, 16>(a, grid, st);
+    case 8018: return go<8, 18>(a, grid, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -17,7 +17,7 @@
 // 3. Shrink and reconstruct without Q and without the rotations: since
 //    B P = (Q U_r) Sigma V_r^T and V_r = Z Sigma^{-1},
 //        D_tau(B) P = (B P) Z diag(g) Z^T,   g_i = (sigma_i - tau)_+ / sigma_i^3,
-//    applied row by row to the ORIGINAL slice (re-read from global memory), a group per
+//    applied row by row to the ORIGINAL slice (re-read from global memory), a warp per
 //    row: y_i = g_i (b . z_i) over the k columns with sigma_i > tau, then
 //    d = sum_i y_i z_i.  2 m n k multiply-adds; the result overwrites the slice.
 #pragma once
@@ -256,11 +256,24 @@ jacobi_svt_kernel(const JArgs a) {
           if (al > T(0) && be > T(0) && g * g > tol2 * al * be) {
             T cs, sn, t;
             rotation_fast(al, be, g, cs, sn, t);
-            const T h = sn / (T(1) + cs);
+            if (sizeof(T) == 4) {
+              // FP32: x' = x - s (y + h x), y' = y + s (x - h y), h = s / (1 + c): the
+              // update is a small increment, so a small rotation adds rounding error of
+              // the size of the increment and stays orthogonal to ~s^2 u.
+              const T h = sn / (T(1) + cs);
 #pragma unroll
-            for (int e = 0; e < E; ++e) {
-              ci[gl + G * e] = fma(-sn, fma(h, x[e], y[e]), x[e]);
-              cj[gl + G * e] = fma(sn, fma(-h, y[e], x[e]), y[e]);
+              for (int e = 0; e < E; ++e) {
+                ci[gl + G * e] = fma(-sn, fma(h, x[e], y[e]), x[e]);
+                cj[gl + G * e] = fma(sn, fma(-h, y[e], x[e]), y[e]);
+              }
+            } else {
+              // FP64: x' = c x - s y, y' = s x + c y (no divide; rounding at 2^-53 per
+              // rotation is far below the FP64 tolerance)
+#pragma unroll
+              for (int e = 0; e < E; ++e) {
+                ci[gl + G * e] = fma(cs, x[e], -sn * y[e]);
+                cj[gl + G * e] = fma(sn, x[e], cs * y[e]);
+              }
             }
             if (gl == 0) {
               nrm2[i] = al - t * g;
@@ -325,55 +338,57 @@ jacobi_svt_kernel(const JArgs a) {
       nrm2[c] = ((sg - tau) / sg) / sg / sg;
     }
     __syncthreads();
-    const int rows_iter = (m + ngrp - 1) / ngrp;
-    for (int it = 0; it < rows_iter; ++it) {  // a group per row of B P
-      const int r = it * ngrp + grp;
+    // a warp per row of B P, lane l holding columns l, l+32, ... (ER per lane)
+    constexpr int ER = (G * E + 31) / 32;
+    const int rows_iter = (m + nwarps - 1) / nwarps;
+    for (int it = 0; it < rows_iter; ++it) {
+      const int r = it * nwarps + warp;
       const bool active = r < m;
-      T b[E];
+      T b[ER];
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int c = gl + G * e;
+      for (int e = 0; e < ER; ++e) {
+        const int c = lane + 32 * e;
         b[e] = T(0);
         if (active && c < n) {
           const int pc = perm[c];
           b[e] = jp.transposed ? A[pc + I1 * r] : A[r + I1 * pc];
         }
       }
-      // y_q = g_q (b . z_q), kept in registers: y_q lives on lane q % G, slot q / G
-      T yreg[E];
+      // y_q = g_q (b . z_q), kept in registers: y_q lives on lane q % 32, slot q / 32
+      T yreg[ER];
 #pragma unroll
-      for (int s2 = 0; s2 < E; ++s2) {
+      for (int s2 = 0; s2 < ER; ++s2) {
         yreg[s2] = T(0);
-        for (int gq = 0; gq < G; ++gq) {
-          const int q = s2 * G + gq;
+        for (int gq = 0; gq < 32; ++gq) {
+          const int q = s2 * 32 + gq;
           if (q < k) {  // uniform over the CTA
             const T* z = W + (size_t)ld * list[q];
             T d = T(0);
 #pragma unroll
-            for (int e = 0; e < E; ++e) d = fma(z[gl + G * e], b[e], d);
-            d = group_sum<G>(d);
-            if (gl == gq) yreg[s2] = d * nrm2[list[q]];
+            for (int e = 0; e < ER; ++e) d = fma(z[lane + 32 * e], b[e], d);
+            d = warp_allsum(d);
+            if (lane == gq) yreg[s2] = d * nrm2[list[q]];
           }
         }
       }
-      T out[E];
+      T out[ER];
 #pragma unroll
-      for (int e = 0; e < E; ++e) out[e] = T(0);
+      for (int e = 0; e < ER; ++e) out[e] = T(0);
 #pragma unroll
-      for (int s2 = 0; s2 < E; ++s2) {
-        for (int gq = 0; gq < G; ++gq) {
-          const int q = s2 * G + gq;
+      for (int s2 = 0; s2 < ER; ++s2) {
+        for (int gq = 0; gq < 32; ++gq) {
+          const int q = s2 * 32 + gq;
           if (q < k) {
-            const T yq = __shfl_sync(0xffffffffu, yreg[s2], gw * G + gq);
+            const T yq = __shfl_sync(0xffffffffu, yreg[s2], gq);
             const T* z = W + (size_t)ld * list[q];
 #pragma unroll
-            for (int e = 0; e < E; ++e) out[e] = fma(yq, z[gl + G * e], out[e]);
+            for (int e = 0; e < ER; ++e) out[e] = fma(yq, z[lane + 32 * e], out[e]);
           }
         }
       }
 #pragma unroll
-      for (int e = 0; e < E; ++e) {
-        const int c = gl + G * e;
+      for (int e = 0; e < ER; ++e) {
+        const int c = lane + 32 * e;
         if (active && c < n) {
           const int pc = perm[c];
           if (jp.transposed) D[pc + I1 * r] = out[e];

@@ -25,7 +25,7 @@ STATUS = {0: "LT_OK", -1: "LT_ERR_ARG", -2: "LT_ERR_SHAPE", -3: "LT_ERR_SINGULAR
 LT_DEV_NOCONV, LT_DEV_NONFINITE, LT_DEV_TIMEOUT = 1, 2, 4
 LT_FP64, LT_FP32, LT_MIXED = 0, 1, 2
 LT_OP_TRANSFORM, LT_OP_INVERSE, LT_OP_PRODUCT, LT_OP_SVD, LT_OP_SVT, LT_OP_PGA = range(6)
-LT_OPT_MAX_SWEEPS, LT_OPT_JACOBI_TOL, LT_OPT_OBJECTIVE, LT_OPT_PROFILE = 0, 1, 2, 3
+LT_OPT_MAX_SWEEPS, LT_OPT_JACOBI_TOL, LT_OPT_OBJECTIVE, LT_OPT_PROFILE, LT_OPT_JACOBI_GROUP = 0, 1, 2, 3, 4
 LT_K_TRANSFORM, LT_K_JACOBI, LT_K_GEMM, LT_K_AUX = 0, 1, 2, 3
 KERNEL_FAMILIES = ("transform", "jacobi", "gemm", "aux")
 
