@@ -216,7 +216,8 @@ def run_ours(args):
     jac_ms_avg = jac["ms"] / jac_launches
     jac_flops_avg = jac["flops"] / jac_launches
     achieved = jac_flops_avg / (jac_ms_avg / 1e3) / 1e9 if jac_ms_avg > 0 else 0.0
-    gpu_launches = sum(v["launches"] for v in st64.values())
+    families = ("transform", "jacobi", "gemm", "aux")
+    gpu_launches = sum(st64[f]["launches"] for f in families)
     slices_per_s = 96 / (jac_ms_avg / 1e3) if jac_ms_avg > 0 else 0.0
 
     # ---------------- FP32 path on the same inputs
@@ -299,9 +300,9 @@ def run_ours(args):
                          "peak_source": "measured FP64 FMA throughput (of measured)",
                          "traffic": None,
                          "flops_per_launch": jac_flops_avg, "ms_per_launch": round(jac_ms_avg, 4)},
-            "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
-                            "share": round(v["ms"] / max(sum(x["ms"] for x in st64.values()), 1e-9), 4)}
-                        for k, v in st64.items()},
+            "kernels": {f: {"launches": st64[f]["launches"], "ms": round(st64[f]["ms"], 3),
+                            "share": round(st64[f]["ms"] / max(sum(st64[x]["ms"] for x in families), 1e-9), 4)}
+                        for f in families},
             "transform_roofline": {
                 "bound": "alu", "achieved": round(tra["flops"] / max(tra["ms"], 1e-9) / 1e6, 2),
                 "unit": "GFLOP/s", "peak": FP64_PEAK_GFLOPS,

@@ -90,8 +90,11 @@ typedef enum {
   LT_OPT_OBJECTIVE = 2,      /* PGA: also accumulate the objective (0/1, default 0) */
   LT_OPT_PROFILE = 3,        /* 1: bracket every kernel launch with CUDA events on its
                                 stream, summed per kernel family by lt_ctx_get_stats */
-  LT_OPT_JACOBI_GROUP = 4    /* SVT kernel: lanes per column pair (8, 16 or 32); 0 (the
+  LT_OPT_JACOBI_GROUP = 4,   /* SVT kernel: lanes per column pair (8, 16 or 32); 0 (the
                                 default) lets the planner choose from min(I1, I2) */
+  LT_OPT_JACOBI_BLOCK = 5    /* SVT kernel: 1 = rotate column pairs straight through
+                                shared memory; 0 (default) = FP32 contexts hold blocks of
+                                2-4 columns per group in registers where they fit */
 } lt_option;
 
 /* Kernel families counted by lt_ctx_get_stats. */
@@ -109,6 +112,13 @@ typedef struct {
 
 typedef struct {
   lt_kernel_stats k[4];
+  /* SVT Jacobi kernel, LT_OPT_PROFILE on: SM clock cycles spent per phase, summed over
+     slices (measured by one thread of each CTA): [0] loading the slice, [1] pivoted
+     QR (all of it), [2] Jacobi sweeps, [3] selecting the singular values above tau,
+     [4] their reconstruction coefficients, [5] the reconstruction of the rows; the QR
+     split into [6] pivot search, [7] column swap, [8] Householder vector, [9] update of
+     the trailing columns. */
+  double jacobi_phase_cycles[10];
 } lt_stats;
 
 typedef struct lt_ctx_s* lt_ctx;

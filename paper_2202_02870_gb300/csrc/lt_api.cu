@@ -153,6 +153,7 @@ cudaError_t run_transform(Ctx& c, const lt::TransformPlan& plan, int64_t S, cons
 cudaError_t run_jacobi(Ctx& c, const lt::JacobiPlan& jp, lt::JacobiIO io, cudaStream_t st) {
   Scope sc(c, st, LT_K_JACOBI);
   io.flops = c.d_counters + LT_K_JACOBI;
+  io.phases = c.profile ? c.d_counters + 4 : nullptr;
   cudaError_t e = lt::launch_jacobi(c, jp, io, st);
   // bytes: read the slices, re-read them for the reconstruction, write the result
   const double n = (double)jp.I1 * jp.I2 * c.P * c.elem;
@@ -309,8 +310,8 @@ lt_status lt_ctx_create(int K, const int64_t* mode_sizes, const double* const* M
   if (e == cudaSuccess) e = cudaMemcpy(c->d_inv, bi.data(), bi.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, sizeof(lt::PgaScalars));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 4 * sizeof(double));
-  if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 4 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 14 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 14 * sizeof(double));
   if (e != cudaSuccess) { lt_ctx_destroy(reinterpret_cast<lt_ctx>(c)); return LT_ERR_CUDA; }
   *out = reinterpret_cast<lt_ctx>(c);
   return LT_OK;
@@ -348,6 +349,10 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
       return LT_OK;
     case LT_OPT_PROFILE:
       c->profile = value != 0.0;
+      return LT_OK;
+    case LT_OPT_JACOBI_BLOCK:
+      if (!(value == 0 || value == 1)) return LT_ERR_ARG;
+      c->jacobi_pairwise = (int)value;
       return LT_OK;
     case LT_OPT_JACOBI_GROUP:
       if (!(value == 0 || value == 8 || value == 16 || value == 32)) return LT_ERR_ARG;
@@ -670,10 +675,11 @@ lt_status lt_ctx_get_stats(lt_ctx ctx, lt_stats* out, int reset) {
     c->pool.push_back(r.b);
   }
   c->pending.clear();
-  double dev[4] = {0, 0, 0, 0};
+  double dev[14] = {};
   if (e == cudaSuccess) e = cudaMemcpy(dev, c->d_counters, sizeof(dev), cudaMemcpyDeviceToHost);
   if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, sizeof(dev));
   for (int i = 0; i < 4; ++i) c->stats.k[i].flops += dev[i];
+  for (int i = 0; i < 10; ++i) c->stats.jacobi_phase_cycles[i] += dev[4 + i];
   *out = c->stats;
   if (reset) c->stats = lt_stats{};
   return cuda_status(e);

@@ -36,12 +36,14 @@ struct Ctx {
   double jacobi_tol = 0.0;            // <= 0: default
   int objective = 0;
   int jacobi_group = 0;               // 0: planner's choice
+  int jacobi_pairwise = 0;            // 1: no register blocking
   // Pinned host staging for asynchronous reports
   void* h_pinned = nullptr;
   // Statistics (lt_ctx_get_stats)
   int profile = 0;
   lt_stats stats = {};
-  double* d_counters = nullptr;       // device: [LT_K_JACOBI] executed Jacobi flops
+  double* d_counters = nullptr;       // device: [LT_K_JACOBI] executed Jacobi flops,
+                                      // [4..13] Jacobi phase cycles (profiling)
   struct EventRec { cudaEvent_t a, b; int fam; };
   std::vector<EventRec> pending;
   std::vector<cudaEvent_t> pool;
@@ -127,6 +129,7 @@ struct JacobiPlan {
   bool w_in_smem = true;
   int E = 1;                            // elements per lane per column chunk
   int G = 32;                           // lanes per column pair (SVT kernel)
+  int B = 1;                            // columns per register block (SVT kernel)
   int threads = 512;
   int smem = 0;
   size_t ws_bytes = 0;                  // scratch bytes (global W, Jacobi V, info)
@@ -152,6 +155,7 @@ struct JacobiIO {
   void* scratch = nullptr;  // jp.ws_bytes
   SliceInfo* info = nullptr;
   double* flops = nullptr;  // device counter of executed flops (atomic, per slice)
+  double* phases = nullptr; // device: 10 phase cycle counters (profiling), or null
 };
 
 cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io,

@@ -423,34 +423,48 @@ int jacobi_grid(const Ctx& c, const JacobiPlan& jp) {
 
 // Group width G (lanes per column pair) and rows per lane E of the SVT kernel, from the
 // instantiated set (rows padded to G E >= n).  Returns false when n is too large.
-bool svt_shape(int n, int elem, int force_g, int* G, int* E) {
-  // instantiated (G, E) per element type; rows padded to G E >= n
-  static const int kF8[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, 16, 18, 20, 24};
-  static const int kF16[] = {14, 16, 18, 20, 24};
-  static const int kF32[] = {14, 16, 18, 20, 24, 28, 32};
-  static const int kD8[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14, 16, 18};
-  static const int kD16[] = {1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 12, 14};
-  static const int kD32[] = {8, 10, 12, 14, 16};
-  auto pick = [](const int* set, int cnt, int need) {
-    for (int i = 0; i < cnt; ++i)
-      if (set[i] >= need) return set[i];
-    return -1;
-  };
+// Instantiated SVT kernel shapes: (G lanes per pair, B columns per register block,
+// E rows per lane), rows padded to G E >= n.  Must match the lt_jacobi_f*.cu files.
+struct SvtShape { int G, B; const int* E; int nE; };
+const int kBlk16x4[] = {1, 2, 3, 4, 5, 6, 7, 8, 9};
+const int kBlk16x2[] = {12, 18};
+const int kBlk32x2[] = {12, 18};
+const int kF8[] = {2, 4, 6, 8, 12, 18, 24};
+const int kF16[] = {16, 24};
+const int kF32[] = {20, 24, 28, 32};
+const int kD8[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 18};
+const int kD16[] = {8, 10, 12, 14};
+const int kD32[] = {8, 12, 16};
+
+int pick_E(const int* set, int cnt, int need) {
+  for (int i = 0; i < cnt; ++i)
+    if (set[i] >= need) return set[i];
+  return -1;
+}
+
+// Choose (G, B, E) for n columns.  force_g != 0 fixes G (pairwise); pairwise != 0
+// disables register blocking.  Returns false when no instantiation holds n.
+bool svt_shape(int n, int elem, int force_g, int pairwise, int* G, int* B, int* E) {
+  if (elem == 4 && !force_g && !pairwise && n <= 576) {
+    if (n <= 144) { *G = 16; *B = 4; *E = pick_E(kBlk16x4, 9, (n + 15) / 16); }
+    else if (n <= 288) { *G = 16; *B = 2; *E = pick_E(kBlk16x2, 2, (n + 15) / 16); }
+    else { *G = 32; *B = 2; *E = pick_E(kBlk32x2, 2, (n + 31) / 32); }
+    return *E > 0;
+  }
+  *B = 1;
   auto try_g = [&](int g) {
     const int need = (n + g - 1) / g;
     if (elem == 4) {
-      if (g == 8) return pick(kF8, 15, need);
-      if (g == 16) return pick(kF16, 5, need);
-      return pick(kF32, 7, need);
+      if (g == 8) return pick_E(kF8, 7, need);
+      if (g == 16) return pick_E(kF16, 2, need);
+      return pick_E(kF32, 4, need);
     }
-    if (g == 8) return pick(kD8, 14, need);
-    if (g == 16) return pick(kD16, 12, need);
-    return pick(kD32, 5, need);
+    if (g == 8) return pick_E(kD8, 12, need);
+    if (g == 16) return pick_E(kD16, 4, need);
+    return pick_E(kD32, 3, need);
   };
-  int g;
-  if (force_g) g = force_g;
-  else if (elem == 4) g = n <= 192 ? 8 : (n <= 384 ? 16 : 32);
-  else g = n <= 144 ? 8 : (n <= 224 ? 16 : 32);
+  int g = force_g ? force_g : (elem == 4 ? (n <= 192 ? 8 : (n <= 384 ? 16 : 32))
+                                         : (n <= 144 ? 8 : (n <= 224 ? 16 : 32)));
   int e = try_g(g);
   if (e < 0 && force_g) return false;
   while (e < 0 && g < 32) { g *= 2; e = try_g(g); }
@@ -487,15 +501,22 @@ lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan
     // QR-preconditioned kernel: Jacobi on the n x n factor R^T, G lanes per column
     // pair holding E rows each, leading dimension >= max(m, G E) and odd (conflict-free
     // transposed stores); as many warps as the pairs of a round need, within the cap.
-    int G = 0, E = 0;
-    if (!svt_shape(jp.n, c.elem, c.jacobi_group, &G, &E)) return LT_ERR_SHAPE;
+    int G = 0, E = 0, B = 1;
+    if (!svt_shape(jp.n, c.elem, c.jacobi_group, c.jacobi_pairwise, &G, &B, &E))
+      return LT_ERR_SHAPE;
     jp.G = G;
+    jp.B = B;
     jp.E = E;
+    if (B > 1) jp.npad = (jp.n + 2 * B - 1) / (2 * B) * (2 * B);
     jp.ld = std::max(jp.m, 32 * ((G * E + 31) / 32)) | 1;
-    const int ppw = 32 / G;
-    const int maxw = (c.elem == 8 ? jac::kMaxThreadsF64 : jac::kMaxThreadsF32) / 32;
-    const int want = (jp.npad / 2 + ppw - 1) / ppw;
-    jp.threads = 32 * std::max(4, std::min(maxw, want));
+    if (B > 1) {
+      jp.threads = jac::kMaxThreadsBlocked;
+    } else {
+      const int ppw = 32 / G;
+      const int maxw = (c.elem == 8 ? jac::kMaxThreadsF64 : jac::kMaxThreadsF32) / 32;
+      const int want = (jp.npad / 2 + ppw - 1) / ppw;
+      jp.threads = 32 * std::max(4, std::min(maxw, want));
+    }
     need = c.elem == 8 ? svt_smem<double>(jp) : svt_smem<float>(jp);
     if (need > (size_t)kSmemOptin - 1024) {
       jp.w_in_smem = false;
@@ -540,11 +561,20 @@ cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io
   a.status = c.d_status;
   const int grid = jacobi_grid(c, jp);
   if (jp.mode == JAC_SVT) {
-    if (c.elem == 8)
-      return jp.G == 8 ? jac::launch_svt_f64_g8(a, grid, st) : jac::launch_svt_f64_g16_32(a, grid, st);
-    if (jp.G == 8)
-      return jp.E <= 8 ? jac::launch_svt_f32_g8_small(a, grid, st) : jac::launch_svt_f32_g8_large(a, grid, st);
-    return jac::launch_svt_f32_g16_32(a, grid, st);
+    // try the translation units in turn; each returns cudaErrorNotSupported for shapes
+    // it does not hold
+    using L = cudaError_t (*)(const JArgs&, int, cudaStream_t);
+    static const L f32[] = {jac::launch_svt_f32_blk_a, jac::launch_svt_f32_blk_b,
+                            jac::launch_svt_f32_blk_c, jac::launch_svt_f32_pw_a,
+                            jac::launch_svt_f32_pw_b};
+    static const L f64[] = {jac::launch_svt_f64_a, jac::launch_svt_f64_b, jac::launch_svt_f64_c};
+    const L* tab = c.elem == 8 ? f64 : f32;
+    const int cnt = c.elem == 8 ? 3 : 5;
+    for (int i = 0; i < cnt; ++i) {
+      const cudaError_t e = tab[i](a, grid, st);
+      if (e != cudaErrorNotSupported) return e;
+    }
+    return cudaErrorNotSupported;
   }
   return c.elem == 8 ? launch_t<double>(a, grid, st) : launch_t<float>(a, grid, st);
 }

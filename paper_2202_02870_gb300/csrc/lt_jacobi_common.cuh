@@ -80,11 +80,16 @@ struct JArgs {
 // SVT kernel launchers by element type and group width (lt_jacobi_f32*.cu, _f64.cu).
 constexpr int kMaxThreadsF32 = 768;
 constexpr int kMaxThreadsF64 = 576;
-cudaError_t launch_svt_f32_g8_small(const JArgs& a, int grid, cudaStream_t st);
-cudaError_t launch_svt_f32_g8_large(const JArgs& a, int grid, cudaStream_t st);
-cudaError_t launch_svt_f32_g16_32(const JArgs& a, int grid, cudaStream_t st);
-cudaError_t launch_svt_f64_g8(const JArgs& a, int grid, cudaStream_t st);
-cudaError_t launch_svt_f64_g16_32(const JArgs& a, int grid, cudaStream_t st);
+constexpr int kMaxThreadsBlocked = 512;  // register-blocked FP32 sweeps: 128 registers
+cudaError_t launch_svt_f32_blk_a(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f32_blk_b(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f32_blk_c(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f32_pw_a(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f32_pw_b(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f64_a(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f64_b(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f64_c(const JArgs& a, int grid, cudaStream_t st);
+// Instantiated (G, B, E) shapes (rows padded to G E): see svt_shape in lt_jacobi.cu.
 
 }  // namespace jac
 }  // namespace lt

@@ -69,7 +69,52 @@ __device__ __forceinline__ void rotation_fast(double al, double be, double g, do
   sn = y * t;
 }
 
-template <typename T, int G, int E, int MAXT>
+template <int G, typename T, int E>
+__device__ __forceinline__ T group_dot(const T (&x)[E], const T (&y)[E]) {
+  T g = T(0);
+#pragma unroll
+  for (int e = 0; e < E; ++e) g = fma(x[e], y[e], g);
+  return g;
+}
+
+// Rotate the register-held columns x, y (E rows per lane) given gamma = x.y over the
+// group and the squared norms nx, ny (updated).  Returns true when a rotation was
+// applied (the pair was not yet orthogonal to the tolerance).
+template <typename T, int E>
+__device__ __forceinline__ bool rotate_regs(T (&x)[E], T (&y)[E], T& nx, T& ny, T g, T tol2) {
+  if (!(nx > T(0) && ny > T(0) && g * g > tol2 * nx * ny)) return false;
+  T cs, sn, t;
+  rotation_fast(nx, ny, g, cs, sn, t);
+  if (sizeof(T) == 4) {
+    const T h = sn / (T(1) + cs);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const T xe = x[e], ye = y[e];
+      x[e] = fma(-sn, fma(h, xe, ye), xe);
+      y[e] = fma(sn, fma(-h, ye, xe), ye);
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const T xe = x[e], ye = y[e];
+      x[e] = fma(cs, xe, -sn * ye);
+      y[e] = fma(sn, xe, cs * ye);
+    }
+  }
+  nx = nx - t * g;
+  ny = ny + t * g;
+  return true;
+}
+
+// Round-robin pairing on n (even) items: item n-1 fixed, the others on a circle.
+__host__ __device__ constexpr int rr_i(int r, int k, int n) {
+  return k == 0 ? n - 1 : (r + k) % (n - 1);
+}
+__host__ __device__ constexpr int rr_j(int r, int k, int n) {
+  return k == 0 ? r : (r - k + n - 1) % (n - 1);
+}
+
+template <typename T, int G, int E, int B, int MAXT>
 __global__ void __launch_bounds__(MAXT)
 jacobi_svt_kernel(const JArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -100,9 +145,12 @@ jacobi_svt_kernel(const JArgs a) {
   T* W = jp.w_in_smem ? Ws
                       : reinterpret_cast<T*>(a.io.scratch) + (size_t)blockIdx.x * ld * np;
 
+  long long tph[7];  // phase boundaries (thread 0, profiling only)
+  long long tqr[4];  // QR sub-phase totals (thread 0, profiling only)
   for (int64_t slice = blockIdx.x; slice < jp.P; slice += gridDim.x) {
     const T* A = Ain + slice * I1 * I2;
     T* D = reinterpret_cast<T*>(a.io.D) + slice * I1 * I2;
+    if (a.io.phases && threadIdx.x == 0) tph[0] = clock64();
     // ---- load B; zero the padding rows and column
     if (!jp.transposed) {
       for (int idx = threadIdx.x; idx < ld * np; idx += blockDim.x) {
@@ -121,6 +169,7 @@ jacobi_svt_kernel(const JArgs a) {
     }
     __syncthreads();
 
+    if (a.io.phases && threadIdx.x == 0) tph[1] = clock64();
     // ---- 1. QR with column pivoting: B P = Q R (R in the upper triangle)
     for (int c = warp; c < n; c += nwarps) {
       const T* col = W + (size_t)ld * c;
@@ -130,6 +179,9 @@ jacobi_svt_kernel(const JArgs a) {
       if (lane == 0) { nrm2[c] = s; ref[c] = s; perm[c] = c; }
     }
     __syncthreads();
+    const bool prof = a.io.phases != nullptr && threadIdx.x == 0;
+    long long tq = prof ? clock64() : 0;
+    if (prof) tqr[0] = tqr[1] = tqr[2] = tqr[3] = 0;
     for (int j = 0; j < n; ++j) {
       if (warp == 0) {  // pivot: the remaining column of largest norm
         T best = T(-1);
@@ -140,6 +192,7 @@ jacobi_svt_kernel(const JArgs a) {
         if (lane == 0) s_piv = bi;
       }
       __syncthreads();
+      if (prof) { const long long t = clock64(); tqr[0] += t - tq; tq = t; }
       const int p = s_piv;
       if (p != j) {
         for (int r = threadIdx.x; r < m; r += blockDim.x) {
@@ -154,6 +207,7 @@ jacobi_svt_kernel(const JArgs a) {
         }
       }
       __syncthreads();
+      if (prof) { const long long t = clock64(); tqr[1] += t - tq; tq = t; }
       if (warp == 0) {  // Householder vector v = x - alpha e_1 of x = B(j:m, j)
         const T* col = W + (size_t)ld * j;
         T s = T(0);
@@ -170,29 +224,60 @@ jacobi_svt_kernel(const JArgs a) {
         }
       }
       __syncthreads();
+      if (prof) { const long long t = clock64(); tqr[2] += t - tq; tq = t; }
       const T alpha = s_alpha, beta = s_beta, v0 = s_v0;
       const T* vj = W + (size_t)ld * j;
-      for (int c = j + 1 + warp; c < n; c += nwarps) {  // B(j:m, c) -= beta v (v . B(j:m, c))
-        T* col = W + (size_t)ld * c;
-        T w = (lane == 0) ? v0 * col[j] : T(0);
-        for (int r = j + 1 + lane; r < m; r += 32) w = fma(vj[r], col[r], w);
-        w = warp_allsum(w) * beta;
-        if (lane == 0) col[j] = fma(-w, v0, col[j]);
-        for (int r = j + 1 + lane; r < m; r += 32) col[r] = fma(-w, vj[r], col[r]);
-        __syncwarp();
-        // downdate the remaining norm; recompute it when cancellation has eaten it
-        const T rjc = col[j];
-        T nn = nrm2[c] - rjc * rjc;
-        if (nn <= T(0.01) * ref[c]) {
-          T s = T(0);
-          for (int r = j + 1 + lane; r < m; r += 32) s = fma(col[r], col[r], s);
-          nn = warp_allsum(s);
-          if (lane == 0) ref[c] = nn;
+      // B(j:m, c) -= beta v (v . B(j:m, c)) for c > j; a warp takes four columns at a
+      // time so that four dot products and reductions are in flight together
+      for (int c0 = j + 1 + 4 * warp; c0 < n; c0 += 4 * nwarps) {
+        T* col[4];
+        T w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + u < n ? c0 + u : c0;  // duplicates are read-only below
+          col[u] = W + (size_t)ld * c;
+          w[u] = (lane == 0) ? v0 * col[u][j] : T(0);
         }
-        if (lane == 0) nrm2[c] = nn > T(0) ? nn : T(0);
+        for (int r = j + 1 + lane; r < m; r += 32) {
+          const T vr = vj[r];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) w[u] = fma(vr, col[u][r], w[u]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] *= beta;
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (c0 + u >= n) continue;  // uniform over the warp
+          T* cu = col[u];
+          if (lane == 0) cu[j] = fma(-w[u], v0, cu[j]);
+          for (int r = j + 1 + lane; r < m; r += 32) cu[r] = fma(-w[u], vj[r], cu[r]);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (c0 + u >= n) continue;
+          const int c = c0 + u;
+          T* cu = col[u];
+          // downdate the remaining norm; recompute it when cancellation has eaten it
+          const T rjc = cu[j];
+          T nn = nrm2[c] - rjc * rjc;
+          if (nn <= T(0.01) * ref[c]) {
+            T sq = T(0);
+            for (int r = j + 1 + lane; r < m; r += 32) sq = fma(cu[r], cu[r], sq);
+            nn = warp_allsum(sq);
+            if (lane == 0) ref[c] = nn;
+          }
+          if (lane == 0) nrm2[c] = nn > T(0) ? nn : T(0);
+        }
       }
       if (threadIdx.x == 0) W[j + (size_t)ld * j] = alpha;
       __syncthreads();
+      if (prof) { const long long t = clock64(); tqr[3] += t - tq; tq = t; }
     }
     // ---- Z = R^T (lower triangular), rows n.. zeroed
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
@@ -208,6 +293,7 @@ jacobi_svt_kernel(const JArgs a) {
     }
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
+    if (a.io.phases && threadIdx.x == 0) tph[2] = clock64();
 
     // ---- 2. one-sided Jacobi on Z (n x n), a group of G lanes per pair
     int sweeps = 0, nrot = 0;
@@ -225,6 +311,89 @@ jacobi_svt_kernel(const JArgs a) {
       }
       __syncthreads();
       int flag = 0;
+      if constexpr (B > 1) {
+        // Blocks of B columns; a group holds a block pair (2B columns) in registers and
+        // performs all B^2 cross rotations (and, in the first block round of the sweep,
+        // the intra-block ones) before writing back: B times fewer passes of the matrix
+        // through shared memory per rotation, B independent rotations per step.
+        const int nb = np / B, cfb = nb - 1;
+        for (int br = 0; br < cfb; ++br) {
+          for (int k0 = 0; k0 < nb / 2; k0 += ngrp) {
+            const int k = k0 + grp;
+            const bool active = k < nb / 2;
+            int bx = 0, by = 0;
+            if (active) {
+              if (k == 0) {
+                bx = cfb;
+                by = br;
+              } else {
+                bx = br + k;
+                if (bx >= cfb) bx -= cfb;
+                by = br - k;
+                if (by < 0) by += cfb;
+              }
+            }
+            T X[B][E], Y[B][E], nx[B], ny[B];
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+              const T* cx = W + (size_t)ld * (bx * B + c);
+              const T* cy = W + (size_t)ld * (by * B + c);
+#pragma unroll
+              for (int e = 0; e < E; ++e) {
+                X[c][e] = active ? cx[gl + G * e] : T(0);
+                Y[c][e] = active ? cy[gl + G * e] : T(0);
+              }
+              nx[c] = active ? nrm2[bx * B + c] : T(0);
+              ny[c] = active ? nrm2[by * B + c] : T(0);
+            }
+            if (br == 0) {  // intra-block pairs, once per sweep
+#pragma unroll
+              for (int r = 0; r < B - 1; ++r) {
+#pragma unroll
+                for (int kk = 0; kk < B / 2; ++kk) {
+                  const int i = rr_i(r, kk, B), j = rr_j(r, kk, B);
+                  T g1 = group_dot<G>(X[i], X[j]), g2 = group_dot<G>(Y[i], Y[j]);
+                  g1 = group_sum<G>(g1);
+                  g2 = group_sum<G>(g2);
+                  if (rotate_regs(X[i], X[j], nx[i], nx[j], g1, tol2)) { flag = 1; nrot += (gl == 0); }
+                  if (rotate_regs(Y[i], Y[j], ny[i], ny[j], g2, tol2)) { flag = 1; nrot += (gl == 0); }
+                }
+              }
+            }
+#pragma unroll
+            for (int q = 0; q < B; ++q) {  // cross pairs (X_i, Y_{(i+q) mod B})
+              T g[B];
+#pragma unroll
+              for (int i = 0; i < B; ++i) g[i] = group_dot<G>(X[i], Y[(i + q) % B]);
+#pragma unroll
+              for (int i = 0; i < B; ++i) g[i] = group_sum<G>(g[i]);
+#pragma unroll
+              for (int i = 0; i < B; ++i)
+                if (rotate_regs(X[i], Y[(i + q) % B], nx[i], ny[(i + q) % B], g[i], tol2)) {
+                  flag = 1;
+                  nrot += (gl == 0);
+                }
+            }
+            if (active) {
+#pragma unroll
+              for (int c = 0; c < B; ++c) {
+                T* cx = W + (size_t)ld * (bx * B + c);
+                T* cy = W + (size_t)ld * (by * B + c);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                  cx[gl + G * e] = X[c][e];
+                  cy[gl + G * e] = Y[c][e];
+                }
+                if (gl == 0) {
+                  nrm2[bx * B + c] = nx[c];
+                  nrm2[by * B + c] = ny[c];
+                }
+              }
+            }
+          }
+          __syncthreads();
+        }
+      } else
       for (int rnd = 0; rnd < cfix; ++rnd) {
         for (int k0 = 0; k0 < npairs; k0 += ngrp) {  // every group of the CTA takes a pair
           const int k = k0 + grp;
@@ -299,6 +468,7 @@ jacobi_svt_kernel(const JArgs a) {
     }
     if (nrot) atomicAdd(&s_rot, nrot);
     __syncthreads();
+    if (a.io.phases && threadIdx.x == 0) tph[3] = clock64();
 
     // ---- 3. shrink and reconstruct
     if (threadIdx.x == 0) {
@@ -316,6 +486,7 @@ jacobi_svt_kernel(const JArgs a) {
       }
       if (st) atomicOr(a.status, st);
       s_count = k;
+      if (a.io.phases) tph[4] = clock64();
       if (a.io.info) {
         a.io.info[slice].sweeps = sweeps;
         a.io.info[slice].rank = k;
@@ -338,6 +509,7 @@ jacobi_svt_kernel(const JArgs a) {
       nrm2[c] = ((sg - tau) / sg) / sg / sg;
     }
     __syncthreads();
+    if (a.io.phases && threadIdx.x == 0) tph[5] = clock64();
     // a warp per row of B P, lane l holding columns l, l+32, ... (ER per lane)
     constexpr int ER = (G * E + 31) / 32;
     const int rows_iter = (m + nwarps - 1) / nwarps;
@@ -359,16 +531,41 @@ jacobi_svt_kernel(const JArgs a) {
 #pragma unroll
       for (int s2 = 0; s2 < ER; ++s2) {
         yreg[s2] = T(0);
-        for (int gq = 0; gq < 32; ++gq) {
-          const int q = s2 * 32 + gq;
-          if (q < k) {  // uniform over the CTA
-            const T* z = W + (size_t)ld * list[q];
-            T d = T(0);
+        const int qn = min(32, k - s2 * 32);  // uniform over the CTA
+        int gq = 0;
+        if constexpr (ER <= 8)
+        for (; gq + 4 <= qn; gq += 4) {  // four independent dot products in flight
+          const T* z0 = W + (size_t)ld * list[s2 * 32 + gq];
+          const T* z1 = W + (size_t)ld * list[s2 * 32 + gq + 1];
+          const T* z2 = W + (size_t)ld * list[s2 * 32 + gq + 2];
+          const T* z3 = W + (size_t)ld * list[s2 * 32 + gq + 3];
+          T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
 #pragma unroll
-            for (int e = 0; e < ER; ++e) d = fma(z[lane + 32 * e], b[e], d);
-            d = warp_allsum(d);
-            if (lane == gq) yreg[s2] = d * nrm2[list[q]];
+          for (int e = 0; e < ER; ++e) {
+            d0 = fma(z0[lane + 32 * e], b[e], d0);
+            d1 = fma(z1[lane + 32 * e], b[e], d1);
+            d2 = fma(z2[lane + 32 * e], b[e], d2);
+            d3 = fma(z3[lane + 32 * e], b[e], d3);
           }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+            d3 += __shfl_xor_sync(0xffffffffu, d3, o);
+          }
+          if (lane == gq) yreg[s2] = d0 * nrm2[list[s2 * 32 + gq]];
+          if (lane == gq + 1) yreg[s2] = d1 * nrm2[list[s2 * 32 + gq + 1]];
+          if (lane == gq + 2) yreg[s2] = d2 * nrm2[list[s2 * 32 + gq + 2]];
+          if (lane == gq + 3) yreg[s2] = d3 * nrm2[list[s2 * 32 + gq + 3]];
+        }
+        for (; gq < qn; ++gq) {
+          const T* z = W + (size_t)ld * list[s2 * 32 + gq];
+          T d = T(0);
+#pragma unroll
+          for (int e = 0; e < ER; ++e) d = fma(z[lane + 32 * e], b[e], d);
+          d = warp_allsum(d);
+          if (lane == gq) yreg[s2] = d * nrm2[list[s2 * 32 + gq]];
         }
       }
       T out[ER];
@@ -376,14 +573,12 @@ jacobi_svt_kernel(const JArgs a) {
       for (int e = 0; e < ER; ++e) out[e] = T(0);
 #pragma unroll
       for (int s2 = 0; s2 < ER; ++s2) {
-        for (int gq = 0; gq < 32; ++gq) {
-          const int q = s2 * 32 + gq;
-          if (q < k) {
-            const T yq = __shfl_sync(0xffffffffu, yreg[s2], gq);
-            const T* z = W + (size_t)ld * list[q];
+        const int qn = min(32, k - s2 * 32);
+        for (int gq = 0; gq < qn; ++gq) {
+          const T yq = __shfl_sync(0xffffffffu, yreg[s2], gq);
+          const T* z = W + (size_t)ld * list[s2 * 32 + gq];
 #pragma unroll
-            for (int e = 0; e < ER; ++e) out[e] = fma(yq, z[lane + 32 * e], out[e]);
-          }
+          for (int e = 0; e < ER; ++e) out[e] = fma(yq, z[lane + 32 * e], out[e]);
         }
       }
 #pragma unroll
@@ -397,6 +592,11 @@ jacobi_svt_kernel(const JArgs a) {
       }
     }
     __syncthreads();
+    if (a.io.phases && threadIdx.x == 0) {
+      tph[6] = clock64();
+      for (int q = 0; q < 6; ++q) atomicAdd(a.io.phases + q, double(tph[q + 1] - tph[q]));
+      for (int q = 0; q < 4; ++q) atomicAdd(a.io.phases + 6 + q, double(tqr[q]));
+    }
   }
 }
 

@@ -25,7 +25,8 @@ STATUS = {0: "LT_OK", -1: "LT_ERR_ARG", -2: "LT_ERR_SHAPE", -3: "LT_ERR_SINGULAR
 LT_DEV_NOCONV, LT_DEV_NONFINITE, LT_DEV_TIMEOUT = 1, 2, 4
 LT_FP64, LT_FP32, LT_MIXED = 0, 1, 2
 LT_OP_TRANSFORM, LT_OP_INVERSE, LT_OP_PRODUCT, LT_OP_SVD, LT_OP_SVT, LT_OP_PGA = range(6)
-LT_OPT_MAX_SWEEPS, LT_OPT_JACOBI_TOL, LT_OPT_OBJECTIVE, LT_OPT_PROFILE, LT_OPT_JACOBI_GROUP = 0, 1, 2, 3, 4
+(LT_OPT_MAX_SWEEPS, LT_OPT_JACOBI_TOL, LT_OPT_OBJECTIVE, LT_OPT_PROFILE, LT_OPT_JACOBI_GROUP,
+ LT_OPT_JACOBI_BLOCK) = 0, 1, 2, 3, 4, 5
 LT_K_TRANSFORM, LT_K_JACOBI, LT_K_GEMM, LT_K_AUX = 0, 1, 2, 3
 KERNEL_FAMILIES = ("transform", "jacobi", "gemm", "aux")
 
@@ -50,7 +51,7 @@ class lt_kernel_stats(C.Structure):
 
 
 class lt_stats(C.Structure):
-    _fields_ = [("k", lt_kernel_stats * 4)]
+    _fields_ = [("k", lt_kernel_stats * 4), ("jacobi_phase_cycles", C.c_double * 10)]
 
 
 SIGNATURES = {
@@ -331,9 +332,14 @@ def lt_ctx_get_stats(ctx, reset: bool = False) -> dict:
     and bytes."""
     st = lt_stats()
     _check("lt_ctx_get_stats", lib().lt_ctx_get_stats(ctx.handle, C.byref(st), int(bool(reset))))
-    return {name: {"launches": int(st.k[i].launches), "ms": float(st.k[i].ms),
-                   "flops": float(st.k[i].flops), "bytes": float(st.k[i].bytes)}
-            for i, name in enumerate(KERNEL_FAMILIES)}
+    out = {name: {"launches": int(st.k[i].launches), "ms": float(st.k[i].ms),
+                  "flops": float(st.k[i].flops), "bytes": float(st.k[i].bytes)}
+           for i, name in enumerate(KERNEL_FAMILIES)}
+    out["jacobi_phase_cycles"] = dict(zip(("load", "qr", "sweeps", "select", "coefficients",
+                                           "rows", "qr_pivot", "qr_swap", "qr_householder",
+                                           "qr_update"),
+                                          [float(v) for v in st.jacobi_phase_cycles]))
+    return out
 
 
 def lt_last_device_status(ctx) -> int:

@@ -202,6 +202,35 @@ def test_svt(prec, shape, transforms, tau):
     assert lt.lt_last_device_status(ctx) == 0
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("group,pairwise", [(0, 0), (0, 1), (8, 0), (16, 0), (32, 0)])
+@pytest.mark.parametrize("shape", [(37, 23), (144, 176), (300, 290)])
+def test_svt_kernel_variants(prec, group, pairwise, shape):
+    """Every instantiated form of the SVT kernel (lanes per pair, register-blocked or
+    pairwise sweeps) against the oracle, on an odd shape, the benchmark's slice shape
+    and a slice that needs the large-column forms."""
+    rng = np.random.default_rng(shape[0])
+    transforms = [("dct", 2)]
+    full = tuple(shape) + (2,)
+    A = rng.standard_normal(full)
+    ctx = make_ctx(transforms, prec)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_GROUP, group)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_BLOCK, pairwise)
+    dt = dtype_of(prec)
+    D = empty_dev(full, dt)
+    max_rows = {lt.LT_FP64: {8: 144, 16: 224, 32: 512}, lt.LT_FP32: {8: 192, 16: 384, 32: 1024}}
+    if group and min(shape) > max_rows[prec][group]:
+        # a forced group width too narrow for the slice is refused, nothing enqueued
+        with pytest.raises(lt.LtError) as err:
+            lt.lt_svt(ctx, to_dev(A, dt), 1.0, D)
+        assert err.value.status == -2
+        return
+    lt.lt_svt(ctx, to_dev(A, dt), 1.0, D)
+    torch.cuda.synchronize()
+    assert rel(from_dev(D, full), O.svt(A, 1.0, oracle_mats(transforms))) <= TOL[prec]
+    assert lt.lt_last_device_status(ctx) == 0
+
+
 # ------------------------------------------------------------------ PGA
 def completion_inputs(c):
     Ms = oracle_mats(c["transforms"])
