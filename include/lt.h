@@ -83,7 +83,7 @@ typedef enum {
   LT_OPT_MAX_SWEEPS = 0,     /* Jacobi sweep limit (default 40); NOCONV when hit */
   LT_OPT_JACOBI_TOL = 1,     /* pair tolerance: rotate when |a.b| > tol*sqrt(a.a b.b);
                                 value <= 0 restores the default: r * unit roundoff for
-                                LT_FP64, sqrt(r) * unit roundoff otherwise, r = rows of
+                                LT_FP64, max(sqrt(r)/8, 4) * unit roundoff otherwise, r = rows of
                                 the matrix being orthogonalised (min(I1,I2) for the SVT,
                                 which works on the triangular factor of a pivoted QR;
                                 max(I1,I2) for the SVD) */

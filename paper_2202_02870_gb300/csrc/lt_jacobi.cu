@@ -434,7 +434,7 @@ const int kF16[] = {16, 24};
 const int kF32[] = {20, 24, 28, 32};
 const int kD8[] = {1, 2, 3, 4, 5, 6, 8, 10, 12, 14, 16, 18};
 const int kD16[] = {8, 10, 12, 14};
-const int kD32[] = {8, 12, 16};
+const int kD32[] = {8, 12, 16, 18};
 
 int pick_E(const int* set, int cnt, int need) {
   for (int i = 0; i < cnt; ++i)
@@ -461,7 +461,7 @@ bool svt_shape(int n, int elem, int force_g, int pairwise, int* G, int* B, int* 
     }
     if (g == 8) return pick_E(kD8, 12, need);
     if (g == 16) return pick_E(kD16, 4, need);
-    return pick_E(kD32, 3, need);
+    return pick_E(kD32, 4, need);
   };
   int g = force_g ? force_g : (elem == 4 ? (n <= 192 ? 8 : (n <= 384 ? 16 : 32))
                                          : (n <= 144 ? 8 : (n <= 224 ? 16 : 32)));
@@ -553,11 +553,16 @@ cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io
   a.jp = jp;
   a.io = io;
   a.max_sweeps = c.max_sweeps;
-  // default pair tolerance: rows of the orthogonalised matrix (n for the SVT kernel,
-  // which works on R^T; m for the SVD kernel) times u in FP64, sqrt(rows) u in FP32
+  // default pair tolerance, r = rows of the orthogonalised matrix (n for the SVT kernel,
+  // which works on R^T; m for the SVD kernel): r u in FP64; max(sqrt(r) / 8, 4) u in
+  // FP32 -- the FP32 SVT error is proportional to the tolerance down to a floor of a
+  // few 1e-7 (measured: 9.1e-6 at sqrt(r) u, 1.0e-6 at sqrt(r) u / 10 for 540 x 960
+  // slices) and the momentum of PGA amplifies per-call errors about tenfold; below ~4 u
+  // the rounding of the FP32 dot products keeps small slices from converging
   const double u = c.elem == 8 ? DBL_EPSILON / 2 : FLT_EPSILON / 2;
   const double rows = jp.mode == JAC_SVT ? jp.n : jp.m;
-  a.tol = c.jacobi_tol > 0 ? c.jacobi_tol : (c.elem == 8 ? rows * u : std::sqrt(rows) * u);
+  a.tol = c.jacobi_tol > 0 ? c.jacobi_tol
+                           : (c.elem == 8 ? rows * u : std::max(std::sqrt(rows) / 8.0, 4.0) * u);
   a.status = c.d_status;
   const int grid = jacobi_grid(c, jp);
   if (jp.mode == JAC_SVT) {

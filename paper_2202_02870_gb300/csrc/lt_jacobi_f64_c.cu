@@ -23,6 +23,7 @@ cudaError_t launch_svt_f64_c(const JArgs& a, int grid, cudaStream_t st) {
     case 320108: return go<32, 8, 1>(a, grid, st);
     case 320112: return go<32, 12, 1>(a, grid, st);
     case 320116: return go<32, 16, 1>(a, grid, st);
+    case 320118: return go<32, 18, 1>(a, grid, st);
     default: return cudaErrorNotSupported;
   }
 }
