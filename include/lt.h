@@ -235,10 +235,15 @@ LT_API lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8
                           void* ws, size_t ws_bytes, void* stream);
 
 /* Many independent completion problems (each with its own context, sizes, mask,
- * observations, tau and step; all contexts of one precision) run together: each
- * stage of an iteration is one launch over all problems' tiles or slices.  ws: one
- * buffer of at least lt_workspace_size_batched bytes.  reports: host array of nprob
- * (may be NULL), written when the stream reaches the end of the work. */
+ * observations, tau and step; all contexts of one precision; cold starts, fixed
+ * iteration count, no tolerance stop) run together: two iterations of every problem
+ * are captured into one CUDA graph with an independent branch per problem, and the
+ * graph is replayed iters/2 times (plus one direct iteration when iters is odd), so the
+ * GPU runs the kernels of different problems concurrently while every problem keeps the
+ * kernel shapes planned for its own sizes.  Results are identical to separate
+ * lt_pga_complete calls.  ws: one buffer of at least lt_workspace_size_batched bytes.
+ * reports: host array of nprob (may be NULL; requires a distinct context per problem),
+ * written when the stream reaches the end of the work. */
 LT_API lt_status lt_workspace_size_batched(int nprob, const lt_ctx* ctxs, const int64_t* I1,
                                     const int64_t* I2, size_t* out);
 LT_API lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const int64_t* I1,

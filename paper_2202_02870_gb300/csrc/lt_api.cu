@@ -114,14 +114,16 @@ struct Scope {
   Ctx& c;
   cudaStream_t st;
   int fam;
+  bool account;
   cudaEvent_t a = nullptr;
-  Scope(Ctx& ctx, cudaStream_t s, int f) : c(ctx), st(s), fam(f) {
-    if (c.profile) {
+  Scope(Ctx& ctx, cudaStream_t s, int f, bool acc = true) : c(ctx), st(s), fam(f), account(acc) {
+    if (c.profile && account) {
       a = take_event(c);
       cudaEventRecord(a, st);
     }
   }
   void done(int64_t launches, double flops, double bytes) {
+    if (!account) return;
     c.stats.k[fam].launches += launches;
     c.stats.k[fam].flops += flops;
     c.stats.k[fam].bytes += bytes;
@@ -150,15 +152,29 @@ cudaError_t run_transform(Ctx& c, const lt::TransformPlan& plan, int64_t S, cons
   return e;
 }
 
-cudaError_t run_jacobi(Ctx& c, const lt::JacobiPlan& jp, lt::JacobiIO io, cudaStream_t st) {
-  Scope sc(c, st, LT_K_JACOBI);
+cudaError_t run_jacobi(Ctx& c, const lt::JacobiPlan& jp, lt::JacobiIO io, cudaStream_t st,
+                       bool account = true) {
+  Scope sc(c, st, LT_K_JACOBI, account);
   io.flops = c.d_counters + LT_K_JACOBI;
-  io.phases = c.profile ? c.d_counters + 4 : nullptr;
+  io.phases = (c.profile && account) ? c.d_counters + 4 : nullptr;
   cudaError_t e = lt::launch_jacobi(c, jp, io, st);
   // bytes: read the slices, re-read them for the reconstruction, write the result
   const double n = (double)jp.I1 * jp.I2 * c.P * c.elem;
   sc.done(1, 0.0, jp.mode == lt::JAC_SVT ? 3 * n : 2 * n);
   return e;
+}
+
+// Destroy executable graphs whose launches have completed.
+void sweep_retired(Ctx& c) {
+  for (size_t i = 0; i < c.retired.size();) {
+    if (cudaEventQuery(c.retired[i].done) == cudaSuccess) {
+      cudaGraphExecDestroy(c.retired[i].exec);
+      cudaEventDestroy(c.retired[i].done);
+      c.retired.erase(c.retired.begin() + i);
+    } else {
+      ++i;
+    }
+  }
 }
 
 // ---- workspace layouts ---------------------------------------------------------------
@@ -327,6 +343,7 @@ lt_status lt_ctx_destroy(lt_ctx ctx) {
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->d_counters) cudaFree(c->d_counters);
   for (auto& r : c->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto& r : c->retired) { cudaGraphExecDestroy(r.exec); cudaEventDestroy(r.done); }
   for (auto ev : c->pool) cudaEventDestroy(ev);
   delete c;
   return LT_OK;
@@ -525,6 +542,149 @@ lt_status lt_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau, 
   return cuda_status(e);
 }
 
+}  // extern "C"
+
+namespace {
+
+// One PGA run (Algorithm 5) split into enqueue steps, so that a batch of runs can be
+// captured into one CUDA graph with a branch per problem.
+struct PgaRun {
+  Ctx* c;
+  PgaLayout L;
+  int64_t I1, I2;
+  double tau, step;
+  size_t bytes;
+  void* X;
+  void* X2;
+  void* Gh;
+  lt::PgaScalars* scal;
+  lt::PgaFuse f;
+  lt::JacobiIO io;
+  double fwd_bytes, inv_bytes, fwd_flops, inv_flops;
+  int rows;
+};
+
+lt_status pga_prepare(Ctx& c, int64_t I1, int64_t I2, const uint8_t* mask, const void* obs,
+                      double tau, double step, void* X, void* ws, size_t ws_bytes,
+                      PgaRun* r) {
+  lt_status s = check_dims(I1, I2);
+  if (s != LT_OK) return s;
+  if ((s = pga_layout(c, I1, I2, &r->L)) != LT_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, r->L.total)) != LT_OK) return s;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  r->c = &c;
+  r->I1 = I1;
+  r->I2 = I2;
+  r->tau = tau;
+  r->step = step;
+  r->bytes = (size_t)I1 * I2 * c.P * c.elem;
+  r->X = X;
+  r->X2 = w + r->L.x2;
+  r->Gh = w + r->L.ghat;
+  r->scal = reinterpret_cast<lt::PgaScalars*>(w + r->L.scal);
+  r->f = lt::PgaFuse();
+  r->f.mask = mask;
+  r->f.obs = obs;
+  r->f.step = step;
+  r->f.scal = r->scal;
+  r->f.partials = reinterpret_cast<double*>(w + r->L.partials);
+  r->f.objective = c.objective;
+  r->io = lt::JacobiIO();
+  r->io.A = r->Gh;
+  r->io.D = r->Gh;
+  r->io.tau = step * tau;
+  r->io.scal = r->scal;
+  r->io.scratch = w + r->L.jac;
+  r->io.info = reinterpret_cast<lt::SliceInfo*>(w + r->L.info);
+  // algorithmic traffic of the fused transforms: forward reads X, X_old, obs, mask and
+  // writes G_hat; inverse reads D_hat, X, X_old (+ mask, obs for the objective) and
+  // writes X_new; intermediate passes read and write the tensor once more each
+  const double Nd = (double)I1 * I2 * c.P, eb = (double)c.elem;
+  r->fwd_bytes = Nd * (4 * eb + 1) + (r->L.fwd.npass - 1) * 2 * Nd * eb;
+  r->inv_bytes = Nd * (4 * eb + (c.objective ? eb + 1 : 0)) + (r->L.inv.npass - 1) * 2 * Nd * eb;
+  r->fwd_flops = transform_flops(r->L.fwd, I1 * I2, c.P) + 6 * Nd;
+  r->inv_flops = transform_flops(r->L.inv, I1 * I2, c.P) + 7 * Nd;
+  r->rows = r->L.max_rows;
+  return LT_OK;
+}
+
+// X^0 = X^1 = X (or the checkpoint), scalars t_0, t_1.
+cudaError_t pga_begin(PgaRun& r, const lt_pga_state* state, double tol, cudaStream_t st) {
+  const bool resume = state && state->k > 0;
+  Scope sc(*r.c, st, LT_K_AUX);
+  cudaError_t e = lt::launch_copy_bytes(r.X2, resume ? state->X_prev : r.X, r.bytes, st);
+  if (e == cudaSuccess)
+    e = lt::launch_pga_init(r.scal, resume ? state->t_prev : 1.0, resume ? state->t : 1.0,
+                            resume ? state->k : 0, tol, st);
+  sc.done(2, 0.0, 2.0 * r.bytes);
+  return e;
+}
+
+// Iteration j of the run: fused forward transform, Jacobi SVT, fused inverse transform,
+// scalar update.  `account` is false while the launches are being captured into a graph
+// (they are then counted per replay).
+cudaError_t pga_iteration(PgaRun& r, int64_t j, cudaStream_t st, bool account) {
+  Ctx& c = *r.c;
+  void* cur = (j % 2 == 0) ? r.X : r.X2;
+  void* old = (j % 2 == 0) ? r.X2 : r.X;
+  r.f.x_cur = cur;
+  r.f.x_old = old;
+  r.f.x_out = old;
+  int rows = 0;
+  cudaError_t e;
+  {
+    Scope sc(c, st, LT_K_TRANSFORM, account);
+    e = lt::launch_transform(c, r.L.fwd, nullptr, r.Gh, lt::FUSE_PGA_FORWARD, &r.f, st, nullptr);
+    sc.done(r.L.fwd.npass, r.fwd_flops, r.fwd_bytes);
+  }
+  if (e == cudaSuccess) e = run_jacobi(c, r.L.jp, r.io, st, account);
+  if (e == cudaSuccess) {
+    Scope sc(c, st, LT_K_TRANSFORM, account);
+    e = lt::launch_transform(c, r.L.inv, r.Gh, r.Gh, lt::FUSE_PGA_INVERSE, &r.f, st, &rows);
+    sc.done(r.L.inv.npass, r.inv_flops, r.inv_bytes);
+  }
+  if (e == cudaSuccess) {
+    Scope sc(c, st, LT_K_AUX, account);
+    e = lt::launch_pga_finish(r.scal, r.f.partials, rows, r.io.info, c.P, r.tau, c.objective,
+                              c.d_status, st);
+    sc.done(1, 0.0, 0.0);
+  }
+  return e;
+}
+
+// Host-side counts of one replayed iteration (graph launches bypass Scope).
+void pga_account_iteration(PgaRun& r) {
+  Ctx& c = *r.c;
+  c.stats.k[LT_K_TRANSFORM].launches += r.L.fwd.npass + r.L.inv.npass;
+  c.stats.k[LT_K_TRANSFORM].flops += r.fwd_flops + r.inv_flops;
+  c.stats.k[LT_K_TRANSFORM].bytes += r.fwd_bytes + r.inv_bytes;
+  c.stats.k[LT_K_JACOBI].launches += 1;
+  c.stats.k[LT_K_JACOBI].bytes += 3.0 * (double)r.I1 * r.I2 * c.P * c.elem;
+  c.stats.k[LT_K_AUX].launches += 1;
+}
+
+cudaError_t pga_end(PgaRun& r, lt_pga_state* state, lt_pga_report* report, cudaStream_t st) {
+  cudaError_t e;
+  {
+    Scope sc(*r.c, st, LT_K_AUX);
+    e = lt::launch_select_result(r.scal, r.X, r.X2, state ? state->X_prev : nullptr, r.bytes, st);
+    sc.done(1, 0.0, 3.0 * r.bytes);
+  }
+  if (e == cudaSuccess && (report || state)) {
+    e = cudaMemcpyAsync(r.c->h_pinned, r.scal, sizeof(lt::PgaScalars), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) {
+      ReportJob* job = new ReportJob{static_cast<const lt::PgaScalars*>(r.c->h_pinned), report, state};
+      e = cudaLaunchHostFunc(st, report_cb, job);
+      if (e != cudaSuccess) delete job;
+    }
+  }
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
 lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8_t* mask,
                           const void* obs, double tau, double step, int64_t iters,
                           double tol, void* X, lt_pga_state* state, lt_pga_report* report,
@@ -533,92 +693,14 @@ lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8_t* mas
   if (!(tau >= 0.0) || !std::isfinite(tau) || !(step > 0.0) || !std::isfinite(step)) return LT_ERR_ARG;
   if (iters < 0 || !(tol >= 0.0)) return LT_ERR_ARG;
   if (state && (state->X_prev == nullptr || state->X_prev == X || state->k < 0)) return LT_ERR_ARG;
-  lt_status s = check_dims(I1, I2);
-  if (s != LT_OK) return s;
   Ctx& c = *reinterpret_cast<Ctx*>(ctx);
-  PgaLayout L;
-  if ((s = pga_layout(c, I1, I2, &L)) != LT_OK) return s;
-  if ((s = check_ws(ws, ws_bytes, L.total)) != LT_OK) return s;
+  PgaRun r;
+  lt_status s = pga_prepare(c, I1, I2, mask, obs, tau, step, X, ws, ws_bytes, &r);
+  if (s != LT_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned char* w = static_cast<unsigned char*>(ws);
-  const size_t bytes = (size_t)I1 * I2 * c.P * c.elem;
-  void* X2 = w + L.x2;
-  void* Gh = w + L.ghat;
-  double* partials = reinterpret_cast<double*>(w + L.partials);
-  lt::PgaScalars* scal = reinterpret_cast<lt::PgaScalars*>(w + L.scal);
-  lt::SliceInfo* info = reinterpret_cast<lt::SliceInfo*>(w + L.info);
-
-  const bool resume = state && state->k > 0;
-  const double Nd = (double)I1 * I2 * c.P;
-  cudaError_t e;
-  {
-    Scope sc(c, st, LT_K_AUX);
-    e = lt::launch_copy_bytes(X2, resume ? state->X_prev : X, bytes, st);
-    if (e == cudaSuccess)
-      e = lt::launch_pga_init(scal, resume ? state->t_prev : 1.0, resume ? state->t : 1.0,
-                              resume ? state->k : 0, tol, st);
-    sc.done(2, 0.0, 2.0 * bytes);
-  }
-  lt::PgaFuse f;
-  f.mask = mask;
-  f.obs = obs;
-  f.step = step;
-  f.scal = scal;
-  f.partials = partials;
-  f.objective = c.objective;
-  lt::JacobiIO io;
-  io.A = Gh;
-  io.D = Gh;
-  io.tau = step * tau;
-  io.scal = scal;
-  io.scratch = w + L.jac;
-  io.info = info;
-  // algorithmic traffic of the fused transforms: forward reads X, X_old, obs, mask and
-  // writes G_hat; inverse reads D_hat, X, X_old (+ mask, obs for the objective) and
-  // writes X_new; intermediate passes read and write the tensor once more each
-  const double eb = (double)c.elem;
-  const double fwd_bytes = Nd * (4 * eb + 1) + (L.fwd.npass - 1) * 2 * Nd * eb;
-  const double inv_bytes = Nd * (4 * eb + (c.objective ? eb + 1 : 0)) + (L.inv.npass - 1) * 2 * Nd * eb;
-  const double fwd_flops = transform_flops(L.fwd, I1 * I2, c.P) + 6 * Nd;
-  const double inv_flops = transform_flops(L.inv, I1 * I2, c.P) + 7 * Nd;
-  for (int64_t j = 0; j < iters && e == cudaSuccess; ++j) {
-    void* cur = (j % 2 == 0) ? X : X2;
-    void* old = (j % 2 == 0) ? X2 : X;
-    f.x_cur = cur;
-    f.x_old = old;
-    f.x_out = old;
-    int rows = 0;
-    {
-      Scope sc(c, st, LT_K_TRANSFORM);
-      e = lt::launch_transform(c, L.fwd, nullptr, Gh, lt::FUSE_PGA_FORWARD, &f, st, nullptr);
-      sc.done(L.fwd.npass, fwd_flops, fwd_bytes);
-    }
-    if (e == cudaSuccess) e = run_jacobi(c, L.jp, io, st);
-    if (e == cudaSuccess) {
-      Scope sc(c, st, LT_K_TRANSFORM);
-      e = lt::launch_transform(c, L.inv, Gh, Gh, lt::FUSE_PGA_INVERSE, &f, st, &rows);
-      sc.done(L.inv.npass, inv_flops, inv_bytes);
-    }
-    if (e == cudaSuccess) {
-      Scope sc(c, st, LT_K_AUX);
-      e = lt::launch_pga_finish(scal, partials, rows, info, c.P, tau, c.objective,
-                                c.d_status, st);
-      sc.done(1, 0.0, 0.0);
-    }
-  }
-  if (e == cudaSuccess) {
-    Scope sc(c, st, LT_K_AUX);
-    e = lt::launch_select_result(scal, X, X2, state ? state->X_prev : nullptr, bytes, st);
-    sc.done(1, 0.0, 3.0 * bytes);
-  }
-  if (e == cudaSuccess && (report || state)) {
-    e = cudaMemcpyAsync(c.h_pinned, scal, sizeof(lt::PgaScalars), cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) {
-      ReportJob* job = new ReportJob{static_cast<const lt::PgaScalars*>(c.h_pinned), report, state};
-      e = cudaLaunchHostFunc(st, report_cb, job);
-      if (e != cudaSuccess) delete job;
-    }
-  }
+  cudaError_t e = pga_begin(r, state, tol, st);
+  for (int64_t j = 0; j < iters && e == cudaSuccess; ++j) e = pga_iteration(r, j, st, true);
+  if (e == cudaSuccess) e = pga_end(r, state, report, st);
   return cuda_status(e);
 }
 
@@ -643,24 +725,92 @@ lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const int64_t* 
                                   lt_pga_report* reports, void* ws, size_t ws_bytes,
                                   void* stream) {
   if (nprob < 1 || !ctxs || !I1 || !I2 || !mask || !obs || !tau || !step || !X) return LT_ERR_ARG;
+  if (iters < 0) return LT_ERR_ARG;
   size_t need = 0;
   lt_status s = lt_workspace_size_batched(nprob, ctxs, I1, I2, &need);
   if (s != LT_OK) return s;
   if ((s = check_ws(ws, ws_bytes, need)) != LT_OK) return s;
-  const lt_precision prec = reinterpret_cast<Ctx*>(ctxs[0])->prec;
-  for (int i = 0; i < nprob; ++i)
-    if (reinterpret_cast<Ctx*>(ctxs[i])->prec != prec) return LT_ERR_ARG;
+  for (int i = 0; i < nprob; ++i) {
+    if (!ctxs[i] || !mask[i] || !obs[i] || !X[i]) return LT_ERR_ARG;
+    if (!(tau[i] >= 0.0) || !std::isfinite(tau[i]) || !(step[i] > 0.0) || !std::isfinite(step[i]))
+      return LT_ERR_ARG;
+    if (reinterpret_cast<Ctx*>(ctxs[i])->prec != reinterpret_cast<Ctx*>(ctxs[0])->prec)
+      return LT_ERR_ARG;
+    for (int j = 0; j < i; ++j)  // one context per problem: report staging is per context
+      if (ctxs[j] == ctxs[i] && reports) return LT_ERR_ARG;
+  }
+  std::vector<PgaRun> runs(nprob);
   unsigned char* w = static_cast<unsigned char*>(ws);
   size_t off = 0;
   for (int i = 0; i < nprob; ++i) {
     size_t b = 0;
     lt_workspace_size(ctxs[i], LT_OP_PGA, I1[i], I2[i], 0, &b);
-    s = lt_pga_complete(ctxs[i], I1[i], I2[i], mask[i], obs[i], tau[i], step[i], iters, 0.0,
-                        X[i], nullptr, reports ? &reports[i] : nullptr, w + off, b, stream);
+    s = pga_prepare(*reinterpret_cast<Ctx*>(ctxs[i]), I1[i], I2[i], mask[i], obs[i], tau[i],
+                    step[i], X[i], w + off, align256(b), &runs[i]);
     if (s != LT_OK) return s;
     off += align256(b);
   }
-  return LT_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Ctx& c0 = *reinterpret_cast<Ctx*>(ctxs[0]);
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < nprob && e == cudaSuccess; ++i) e = pga_begin(runs[i], nullptr, 0.0, st);
+
+  // Capture two iterations of every problem as independent branches of one graph (two,
+  // so that the ping-pong buffers are back in place at the end of each replay), then
+  // replay it; the GPU runs the branches of different problems concurrently.
+  const int64_t pairs = iters / 2;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess && pairs > 0) {
+    const int ns = std::min(nprob, 32);
+    std::vector<cudaStream_t> cs(ns, nullptr);
+    std::vector<cudaEvent_t> ev(nprob + 1, nullptr);
+    for (int i = 0; i < ns && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&cs[i], cudaStreamNonBlocking);
+    for (int i = 0; i <= nprob && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    cudaGraph_t graph = nullptr;
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(cs[0], cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t ce = cudaEventRecord(ev[nprob], cs[0]);  // fork point
+      for (int i = 0; i < nprob && ce == cudaSuccess; ++i) {
+        cudaStream_t si = cs[i % ns];
+        if (i % ns != 0) ce = cudaStreamWaitEvent(si, ev[nprob], 0);
+        for (int64_t j = 0; j < 2 && ce == cudaSuccess; ++j) ce = pga_iteration(runs[i], j, si, false);
+        if (ce == cudaSuccess) ce = cudaEventRecord(ev[i], si);
+      }
+      for (int i = 0; i < nprob && ce == cudaSuccess; ++i) ce = cudaStreamWaitEvent(cs[0], ev[i], 0);  // join
+      e = cudaStreamEndCapture(cs[0], &graph);
+      if (e == cudaSuccess) e = ce;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    for (auto x : cs) if (x) cudaStreamDestroy(x);
+    for (auto x : ev) if (x) cudaEventDestroy(x);
+    for (int64_t p = 0; p < pairs && e == cudaSuccess; ++p) {
+      e = cudaGraphLaunch(exec, st);
+      for (int i = 0; i < nprob; ++i) {
+        pga_account_iteration(runs[i]);
+        pga_account_iteration(runs[i]);
+      }
+    }
+  }
+  if (e == cudaSuccess && (iters % 2))  // an odd last iteration, directly
+    for (int i = 0; i < nprob && e == cudaSuccess; ++i) e = pga_iteration(runs[i], iters - 1, st, true);
+  for (int i = 0; i < nprob && e == cudaSuccess; ++i)
+    e = pga_end(runs[i], nullptr, reports ? &reports[i] : nullptr, st);
+  if (exec) {
+    // destroy the executable graph once its launches have completed: retire it behind an
+    // event and sweep the retired ones whose event has fired
+    cudaEvent_t done = nullptr;
+    if (cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventRecord(done, st) == cudaSuccess) {
+      c0.retired.push_back({exec, done});
+    } else {
+      cudaStreamSynchronize(st);
+      cudaGraphExecDestroy(exec);
+      if (done) cudaEventDestroy(done);
+    }
+  }
+  sweep_retired(c0);
+  return cuda_status(e);
 }
 
 lt_status lt_ctx_get_stats(lt_ctx ctx, lt_stats* out, int reset) {

@@ -47,6 +47,8 @@ struct Ctx {
   struct EventRec { cudaEvent_t a, b; int fam; };
   std::vector<EventRec> pending;
   std::vector<cudaEvent_t> pool;
+  struct Retired { cudaGraphExec_t exec; cudaEvent_t done; };
+  std::vector<Retired> retired;       // batched-PGA graphs awaiting destruction
 };
 
 // ----------------------------------------------------------------------------------

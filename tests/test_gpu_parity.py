@@ -360,3 +360,84 @@ def test_host_helpers_match_golden_and_oracle():
     for n in (1, 5, 32, 120):
         assert np.abs(lt.lt_make_dct(n) - O.dct_matrix(n)).max() < 1e-14
         assert np.abs(lt.lt_make_cproduct(n) - O.cproduct_matrix(n)).max() < 1e-11
+
+
+# ------------------------------------------------------------------ batched PGA
+def batch_problems(specs, prec, rng_seed=40):
+    """specs: list of (I1, I2, trailing, rank, rho, tau).  Returns contexts, device
+    masks/obs, taus and the host obs/mask (oracle inputs)."""
+    out = []
+    for i, (I1, I2, trailing, rank, rho, tau) in enumerate(specs):
+        c = synth.completion_case(rng_seed, I1, I2, trailing, rank=rank, rho=rho, problem=i)
+        Ms = oracle_mats(c["transforms"])
+        X = O.product(c["U"], O.transpose(c["V"], Ms), Ms)
+        obs = c["mask"] * (X + c["noise"])
+        out.append({"ctx": make_ctx(c["transforms"], prec), "mask": c["mask"], "obs": obs,
+                    "Ms": Ms, "tau": tau})
+    return out
+
+
+def run_batched(probs, prec, iters):
+    dt = dtype_of(prec)
+    Xs = [to_dev(np.zeros(p["obs"].shape), dt) for p in probs]
+    reps = []
+    lt.lt_pga_complete_batched([p["ctx"] for p in probs], [to_dev(p["mask"]) for p in probs],
+                               [to_dev(p["obs"], dt) for p in probs], [p["tau"] for p in probs],
+                               [1.0] * len(probs), iters, Xs, reports=reps)
+    torch.cuda.synchronize()
+    return Xs, reps[0]
+
+
+SMALL_BATCH = [(24, 20, (3, 4), 3, 0.4, 0.3), (40, 18, (3, 8), 2, 0.3, 0.2),
+               (17, 33, (3, 2), 4, 0.5, 0.5), (64, 48, (3, 8), 5, 0.25, 0.4),
+               (9, 12, (3, 16), 2, 0.45, 0.1)]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pga_batched_equals_single_runs(prec):
+    """The batch (one CUDA graph with a branch per problem) gives exactly what separate
+    lt_pga_complete calls give: same kernels, fixed-order reductions (7 iterations: three
+    graph replays and one direct iteration)."""
+    probs = batch_problems(SMALL_BATCH, prec)
+    Xs, reps = run_batched(probs, prec, 7)
+    dt = dtype_of(prec)
+    for p, Xb, rep in zip(probs, Xs, reps):
+        Xs1 = to_dev(np.zeros(p["obs"].shape), dt)
+        lt.lt_pga_complete(p["ctx"], to_dev(p["mask"]), to_dev(p["obs"], dt), p["tau"], 1.0, 7, Xs1)
+        torch.cuda.synchronize()
+        assert torch.equal(Xb, Xs1)
+        assert rep.iters_done == 7 and rep.device_status == 0
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pga_batched_vs_oracle(prec):
+    probs = batch_problems(SMALL_BATCH[:3], prec)
+    Xs, _ = run_batched(probs, prec, 10)
+    for p, Xb in zip(probs, Xs):
+        ref, _ = O.pga(p["mask"], p["obs"], p["tau"], 1.0, 10, p["Ms"])
+        assert rel(from_dev(Xb, p["obs"].shape), ref) <= TOL[prec]
+
+
+def test_pga_batched_config4_full():
+    """The 64-problem batch of uneven sizes (I1 x I2 from 64 x 48 to 512 x 384, I3 = 3,
+    I4 in {8, 16, 32, 64}), FP32: every problem completes its iterations without device
+    errors, and two of them equal their single-problem runs bit for bit."""
+    shapes = synth.config4_shapes()
+    rng = np.random.default_rng(4)
+    ctxs, masks, obss, Xs = [], [], [], []
+    for i, sh in enumerate(shapes):
+        full = (sh["I1"], sh["I2"]) + sh["trailing"]
+        ctxs.append(make_ctx([("dct", n) for n in sh["trailing"]], lt.LT_FP32))
+        m = (rng.random(full) < sh["rho"]).astype(np.uint8)
+        masks.append(to_dev(m))
+        obss.append(to_dev(m * rng.standard_normal(full), torch.float32))
+        Xs.append(torch.zeros(tuple(reversed(full)), dtype=torch.float32, device="cuda"))
+    reps = []
+    lt.lt_pga_complete_batched(ctxs, masks, obss, [0.5] * 64, [1.0] * 64, 4, Xs, reports=reps)
+    torch.cuda.synchronize()
+    assert all(r.iters_done == 4 and r.device_status == 0 for r in reps[0])
+    for i in (0, 37):
+        X1 = torch.zeros_like(Xs[i])
+        lt.lt_pga_complete(ctxs[i], masks[i], obss[i], 0.5, 1.0, 4, X1)
+        torch.cuda.synchronize()
+        assert torch.equal(Xs[i], X1)
