@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 METRIC = "PGA iters/s & L-SVT slices/s, mixed vs FP64 at rel-err<=1e-5; %roofline"
 WORKLOAD = "pga_completion_144x176x3x32_fp64"
 FP64_PEAK_GFLOPS = 1199.4   # measured FP64 FMA throughput of this GB300 pool (probe in DESIGN)
+FP32_PEAK_GFLOPS = 74944.4  # measured FP32 FMA throughput (same probe)
 ORACLE_ITERS_PER_STEP = 3
 
 
@@ -166,6 +167,9 @@ def run_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     def run_path(ctx, obs, dt, K, W, profile):
+        """W warm-up steps, then K timed steps; with `profile` the library brackets every
+        kernel launch of the timed steps with CUDA events on its stream (per-kernel times
+        and rooflines over the timed region)."""
         X = torch.zeros(tshape, dtype=dt, device=dev)
         wsb = torch.empty(lt.lt_workspace_size(ctx, lt.LT_OP_PGA, 144, 176), dtype=torch.uint8, device=dev)
         rep = lt.lt_pga_report()
@@ -196,6 +200,7 @@ def run_ours(args):
         ms = [a.elapsed_time(b) for a, b in times]
         stats = lt.lt_ctx_get_stats(ctx, reset=True)
         lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 0)
+        stats["timed_launches"] = sum(stats[f]["launches"] for f in ("transform", "jacobi", "gemm", "aux"))
         return X, ms, wall, stats, rep
 
     # ---------------- FP64 path (value) with clocks and the Jacobi roofline
@@ -217,7 +222,7 @@ def run_ours(args):
     jac_flops_avg = jac["flops"] / jac_launches
     achieved = jac_flops_avg / (jac_ms_avg / 1e3) / 1e9 if jac_ms_avg > 0 else 0.0
     families = ("transform", "jacobi", "gemm", "aux")
-    gpu_launches = sum(st64[f]["launches"] for f in families)
+    gpu_launches = st64["timed_launches"]  # launches of the K timed steps
     slices_per_s = 96 / (jac_ms_avg / 1e3) if jac_ms_avg > 0 else 0.0
 
     # ---------------- FP32 path on the same inputs
@@ -227,6 +232,14 @@ def run_ours(args):
     rel32 = float(torch.linalg.norm(X32.double() - X64) / torch.linalg.norm(X64))
     j32 = st32["jacobi"]
     j32_ms = j32["ms"] / max(j32["launches"], 1)
+
+    j32_flops = j32["flops"] / max(j32["launches"], 1)
+    j32_achieved = j32_flops / (j32_ms / 1e3) / 1e9 if j32_ms > 0 else 0.0
+
+    # ---------------- batched: the 64 uneven problems of one batch, FP32
+    batched = None
+    if args.batched_steps > 0:
+        batched = run_batched_leg(args, dev, ws)
 
     # ---------------- e2e: host buffers through the C ABI, copies inside each step
     mask_h = torch.from_numpy(np.ascontiguousarray(c["mask"].ravel(order="F"))).reshape(tshape).pin_memory()
@@ -238,6 +251,7 @@ def run_ours(args):
     wse = torch.empty(lt.lt_workspace_size(ctx64, lt.LT_OP_PGA, 144, 176), dtype=torch.uint8, device=dev)
     e2e_ms = []
     st = torch.cuda.current_stream()
+    lt.lt_ctx_set_option(ctx64, lt.LT_OPT_PROFILE, 1)  # same conditions as the timed steps
     for _ in range(max(1, args.steps // 2)):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -250,6 +264,8 @@ def run_ours(args):
         e1.record(st)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
+    lt.lt_ctx_set_option(ctx64, lt.LT_OPT_PROFILE, 0)
+    lt.lt_ctx_get_stats(ctx64, reset=True)
     e2e_step = statistics.mean(e2e_ms)
     if ws > 1:
         t = torch.tensor([e2e_step], device=dev, dtype=torch.float64)
@@ -293,7 +309,12 @@ def run_ours(args):
             "mixed": {"dtype": "f32", "value": round(ws * iters / (mixed_ms / 1e3), 3),
                       "unit": "iters/s", "ms_per_step": round(mixed_ms, 3),
                       "rel_err_vs_fp64": rel32,
-                      "svt_slices_per_s": round(96 / (j32_ms / 1e3), 1) if j32_ms > 0 else None},
+                      "svt_slices_per_s": round(96 / (j32_ms / 1e3), 1) if j32_ms > 0 else None,
+                      "roofline": {"kernel": "jacobi_svt (FP32)", "bound": "alu",
+                                   "achieved": round(j32_achieved, 1), "peak": FP32_PEAK_GFLOPS,
+                                   "unit": "GFLOP/s", "frac": round(j32_achieved / FP32_PEAK_GFLOPS, 4),
+                                   "peak_source": "measured FP32 FMA throughput (of measured)"}},
+            "batched": batched,
             "roofline": {"kernel": "jacobi_svt (FP64)", "bound": "alu",
                          "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
                          "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
@@ -320,6 +341,55 @@ def run_ours(args):
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def run_batched_leg(args, dev, ws):
+    """The 64 independent completion problems of uneven sizes (I1 x I2 from 64 x 48 to
+    512 x 384, I3 = 3, I4 in {8, 16, 32, 64}, DCT transforms), FP32: one
+    lt_pga_complete_batched call (a CUDA graph with a branch per problem) of `iters`
+    iterations per step, against the same problems issued one after the other."""
+    import torch
+    from paper_2202_02870_gb300 import lt, synth
+    shapes = synth.config4_shapes()
+    rng = np.random.default_rng(4)
+    ctxs, masks, obss, Xs = [], [], [], []
+    elems = 0
+    for sh in shapes:
+        full = (sh["I1"], sh["I2"]) + sh["trailing"]
+        elems += int(np.prod(full))
+        ctxs.append(lt.Context(list(sh["trailing"]), [lt.lt_make_dct(n) for n in sh["trailing"]],
+                               lt.LT_FP32))
+        m = torch.from_numpy((rng.random(int(np.prod(full))) < sh["rho"]).astype(np.uint8))
+        masks.append(m.reshape(tuple(reversed(full))).to(dev))
+        obss.append(masks[-1].float() * torch.randn(tuple(reversed(full)), device=dev))
+        Xs.append(torch.zeros(tuple(reversed(full)), dtype=torch.float32, device=dev))
+    n = len(ctxs)
+    iters = args.batched_iters
+    wsb = torch.empty(lt.lt_workspace_size_batched(ctxs, [x.shape[-1] for x in Xs],
+                                                   [x.shape[-2] for x in Xs]),
+                      dtype=torch.uint8, device=dev)
+    run = lambda: lt.lt_pga_complete_batched(ctxs, masks, obss, [0.5] * n, [1.0] * n, iters, Xs, ws=wsb)
+    run()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.batched_steps):
+        run()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) / args.batched_steps
+    # the same work, one problem after the other on one stream
+    e0.record(st)
+    for i in range(n):
+        lt.lt_pga_complete(ctxs[i], masks[i], obss[i], 0.5, 1.0, iters, Xs[i])
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_s = e0.elapsed_time(e1)
+    return {"problems": n, "elements": elems, "iters_per_step": iters, "dtype": "f32",
+            "value": round(ws * n * iters / (ms_b / 1e3), 2), "unit": "problem-iters/s",
+            "ms_per_step": round(ms_b, 2), "sequential_ms": round(ms_s, 2),
+            "speedup_vs_sequential": round(ms_s / ms_b, 3)}
 
 
 def run_case(args):
@@ -405,6 +475,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-iters", type=int, default=15)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batched-steps", type=int, default=2,
+                    help="timed calls of the 64-problem batch (0 skips the batched leg)")
+    ap.add_argument("--batched-iters", type=int, default=4,
+                    help="PGA iterations per call of the 64-problem batch")
     ap.add_argument("--case", default="pga", choices=["pga", "svt", "product"],
                     help="pga: the benchmark line; svt/product: single-operation runs "
                          "used for profiling")
