@@ -479,6 +479,7 @@ size_t svt_smem(const JacobiPlan& jp) {
   size_t b = 0;
   if (jp.w_in_smem) b += sizeof(T) * (size_t)jp.ld * jp.npad;
   b += sizeof(T) * 2 * (size_t)jp.npad + sizeof(int) * 2 * (size_t)jp.npad;
+  if (sizeof(T) == 8) b += sizeof(T) * 2 * (size_t)jp.npad;  // column scales (FP64 sweeps)
   return (b + 15) & ~size_t(15);
 }
 

@@ -54,9 +54,19 @@ __device__ __forceinline__ void rotation(float al, float be, float g, float& cs,
   cs = rsqrtf(1.f + t * t);
   sn = cs * t;
 }
+// zeta = (beta - alpha) / (2 gamma) in FP32 when the operands are inside FP32's range,
+// else by an FP64 divide (rare: slices are scaled to a maximum entry in [1, 2), so this
+// takes only columns below about 1e-19 of it).
+__device__ __forceinline__ float jacobi_zeta(double al, double be, double g) {
+  const float df = float(be - al), gf = float(g);
+  if (fabsf(gf) >= FLT_MIN && fabsf(gf) <= 1e37f && fabsf(df) <= 1e37f)
+    return __fdividef(df, 2.f * gf);
+  return float((be - al) / (2.0 * g));
+}
+
 __device__ __forceinline__ void rotation(double al, double be, double g, double& cs,
                                          double& sn, double& t) {
-  const float zeta = float(be - al) / (2.f * float(g));
+  const float zeta = jacobi_zeta(al, be, g);
   const float az = fabsf(zeta);
   float tf = (az > 1e15f) ? 0.5f / az : 1.f / (az + sqrtf(1.f + az * az));
   if (zeta < 0.f) tf = -tf;
@@ -67,6 +77,20 @@ __device__ __forceinline__ void rotation(double al, double be, double g, double&
   y = y * fma(-0.5 * x, y * y, 1.5);
   cs = y;
   sn = y * t;
+}
+
+// Power of two s with s * maxabs in [1, 2) (in [2, 4) for maxabs in the top binade; 1 when
+// maxabs is zero, subnormal, infinite or NaN).  Scaling a slice by s is exact and keeps the Jacobi arithmetic (squared norms,
+// the FP32 rotation angle) inside the floating-point range whatever the data's scale.
+__device__ __forceinline__ double pow2_scale(double maxabs) {
+  const long long e = (__double_as_longlong(maxabs) >> 52) & 0x7ff;
+  if (e == 0 || e == 0x7ff) return 1.0;
+  return __longlong_as_double((long long)(e < 2046 ? 2046 - e : 1) << 52);
+}
+__device__ __forceinline__ float pow2_scale(float maxabs) {
+  const int e = (__float_as_int(maxabs) >> 23) & 0xff;
+  if (e == 0 || e == 0xff) return 1.f;
+  return __int_as_float((e < 254 ? 254 - e : 1) << 23);
 }
 
 struct JArgs {

@@ -36,6 +36,21 @@ __device__ __forceinline__ T group_sum(T v) {
   return v;
 }
 
+// |v| as an unsigned integer with the same ordering (for a maximum without FP64 compares)
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ unsigned long long abs_bits(float v) {
+  return (unsigned long long)(__float_as_uint(v) & 0x7fffffffu);
+}
+template <typename T> __device__ __forceinline__ T from_abs_bits(unsigned long long b);
+template <> __device__ __forceinline__ double from_abs_bits<double>(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+template <> __device__ __forceinline__ float from_abs_bits<float>(unsigned long long b) {
+  return __uint_as_float((unsigned)b);
+}
+
 // Fast rotation parameters.  FP32: approximate divides and square roots for the angle
 // (it only steers convergence) and one Newton step on c = (1 + t^2)^{-1/2}, so that
 // c^2 + s^2 = 1 to about one unit roundoff.  FP64: the FP32 angle, then two FP64 Newton
@@ -55,7 +70,7 @@ __device__ __forceinline__ void rotation_fast(float al, float be, float g, float
 }
 __device__ __forceinline__ void rotation_fast(double al, double be, double g, double& cs,
                                               double& sn, double& t) {
-  const float zeta = __fdividef(float(be - al), 2.f * float(g));
+  const float zeta = jacobi_zeta(al, be, g);
   const float az = fabsf(zeta);
   const float q = fmaf(az, az, 1.f);
   float tf = (az > 1e15f) ? __fdividef(0.5f, az) : __fdividef(1.f, az + q * rsqrtf(q));
@@ -67,6 +82,24 @@ __device__ __forceinline__ void rotation_fast(double al, double be, double g, do
   y = y * fma(-0.5 * x, y * y, 1.5);
   cs = y;
   sn = y * t;
+}
+
+// FP64 rotation for scaled columns: the tangent t as in rotation_fast, c = (1+t^2)^{-1/2}
+// by two FP64 Newton steps, and 1/c = (1 + t^2) c.
+__device__ __forceinline__ void rotation_scaled(double al, double be, double g, double& cs,
+                                                double& ic, double& t) {
+  const float zeta = jacobi_zeta(al, be, g);
+  const float az = fabsf(zeta);
+  const float q = fmaf(az, az, 1.f);
+  float tf = (az > 1e15f) ? __fdividef(0.5f, az) : __fdividef(1.f, az + q * rsqrtf(q));
+  if (zeta < 0.f) tf = -tf;
+  t = double(tf);
+  const double x = fma(t, t, 1.0);
+  double y = double(rsqrtf(float(x)));
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  y = y * fma(-0.5 * x, y * y, 1.5);
+  cs = y;
+  ic = x * y;
 }
 
 template <int G, typename T, int E>
@@ -129,7 +162,7 @@ jacobi_svt_kernel(const JArgs a) {
   const int gl = lane % G, gw = lane / G;       // lane in group, group in warp
   const int grp = warp * PPW + gw, ngrp = nwarps * PPW;
   const T tol2 = T(a.tol) * T(a.tol);
-  const T tau = T(a.io.tau);
+  const T tau_in = T(a.io.tau);
 
   unsigned char* sp = smem_raw;
   T* Ws = nullptr;
@@ -138,7 +171,16 @@ jacobi_svt_kernel(const JArgs a) {
   T* ref = reinterpret_cast<T*>(sp); sp += sizeof(T) * np;
   int* perm = reinterpret_cast<int*>(sp); sp += sizeof(int) * np;
   int* list = reinterpret_cast<int*>(sp); sp += sizeof(int) * np;
+  // FP64 sweeps keep column i as d_i * (stored column); dsc = d, isc = 1/d
+  constexpr bool kScaled = sizeof(T) == 8 && B == 1;
+  T* dsc = nullptr;
+  T* isc = nullptr;
+  if constexpr (kScaled) {
+    dsc = reinterpret_cast<T*>(sp); sp += sizeof(T) * np;
+    isc = reinterpret_cast<T*>(sp); sp += sizeof(T) * np;
+  }
   __shared__ int s_piv, s_count, s_rot;
+  __shared__ unsigned long long s_maxbits;
   __shared__ T s_alpha, s_beta, s_v0;
 
   const T* Ain = reinterpret_cast<const T*>(a.io.A);
@@ -167,6 +209,29 @@ jacobi_svt_kernel(const JArgs a) {
         if (r >= m || c >= n) W[idx] = T(0);
       }
     }
+    if (threadIdx.x == 0) s_maxbits = 0ULL;
+    __syncthreads();
+    // ---- scale by a power of two (exact) so that the largest entry lies in [1, 2):
+    // D_tau(B) = D_{s tau}(s B) / s, and the reconstruction below, which re-reads the
+    // unscaled slice, needs no correction (Z and g scale by s and 1/s^2)
+    {
+      unsigned long long mb = 0ULL;
+      for (int idx = threadIdx.x; idx < ld * np; idx += blockDim.x) {
+        const unsigned long long v = abs_bits(W[idx]);
+        mb = v > mb ? v : mb;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, mb, o);
+        mb = v > mb ? v : mb;
+      }
+      if (lane == 0) atomicMax(&s_maxbits, mb);
+    }
+    __syncthreads();
+    const T sc = pow2_scale(from_abs_bits<T>(s_maxbits));
+    if (sc != T(1))
+      for (int idx = threadIdx.x; idx < ld * np; idx += blockDim.x) W[idx] *= sc;
+    const T tau = tau_in * sc;
     __syncthreads();
 
     if (a.io.phases && threadIdx.x == 0) tph[1] = clock64();
@@ -291,24 +356,44 @@ jacobi_svt_kernel(const JArgs a) {
       const int r = n + idx % (ld - n), c = idx / (ld - n);
       W[r + (size_t)ld * c] = T(0);
     }
+    if constexpr (kScaled)
+      for (int c = threadIdx.x; c < np; c += blockDim.x) { dsc[c] = T(1); isc[c] = T(1); }
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     if (a.io.phases && threadIdx.x == 0) tph[2] = clock64();
 
     // ---- 2. one-sided Jacobi on Z (n x n), a group of G lanes per pair
+    // Squared column norms, a group per column; scaled columns are first multiplied out
+    // (d_i <- 1), so that the scales stay bounded and Z is in true units afterwards.
+    auto column_norms = [&]() {
+      for (int c0 = 0; c0 < np; c0 += ngrp) {  // trip count uniform over the warp
+        const int c = c0 + grp;
+        T* col = W + (size_t)ld * (c < np ? c : 0);
+        T s = T(0);
+        if constexpr (kScaled) {
+          const T dc = c < np ? dsc[c] : T(1);
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const T v = col[gl + G * e] * dc;
+            if (c < np) col[gl + G * e] = v;
+            s = fma(v, v, s);
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < E; ++e) s = fma(col[gl + G * e], col[gl + G * e], s);
+        }
+        s = group_sum<G>(s);
+        if (gl == 0 && c < np) {
+          nrm2[c] = s;
+          if constexpr (kScaled) { dsc[c] = T(1); isc[c] = T(1); }
+        }
+      }
+    };
     int sweeps = 0, nrot = 0;
     bool rotated = true;
     const int npairs = np / 2, cfix = np - 1;
     while (rotated && sweeps < a.max_sweeps) {
-      for (int c0 = 0; c0 < np; c0 += ngrp) {  // trip count uniform over the warp
-        const int c = c0 + grp;
-        const T* col = W + (size_t)ld * (c < np ? c : 0);
-        T s = T(0);
-#pragma unroll
-        for (int e = 0; e < E; ++e) s = fma(col[gl + G * e], col[gl + G * e], s);
-        s = group_sum<G>(s);
-        if (gl == 0 && c < np) nrm2[c] = s;
-      }
+      column_norms();
       __syncthreads();
       int flag = 0;
       if constexpr (B > 1) {
@@ -422,6 +507,53 @@ jacobi_svt_kernel(const JArgs a) {
           }
           g = group_sum<G>(g);
           const T al = active ? nrm2[i] : T(0), be = active ? nrm2[j] : T(0);
+          if constexpr (kScaled) {
+            // columns d_i x~, d_j y~: the rotation x' = c (x - t y), y' = c (y + t x)
+            // becomes x~' = x~ - t (d_j / d_i) y~, y~' = y~ + t (d_i / d_j) x~ with
+            // d_i' = c d_i, d_j' = c d_j: two FP64 multiply-adds per row instead of four
+            // (Rutishauser-style scaled rotations; the scales are multiplied out at each
+            // sweep start and whenever one falls below 2^-64)
+            const T di = dsc[i], dj = dsc[j];
+            g *= di * dj;
+            if (al > T(0) && be > T(0) && g * g > tol2 * al * be) {
+              T cs, ic, t;
+              rotation_scaled(al, be, g, cs, ic, t);
+              const T ei = isc[i], ej = isc[j];
+              const T alpha = t * dj * ei, beta = t * di * ej;
+              T di2 = di * cs, dj2 = dj * cs, ei2 = ei * ic, ej2 = ej * ic;
+#pragma unroll
+              for (int e = 0; e < E; ++e) {
+                const T xe = x[e], ye = y[e];
+                x[e] = fma(-alpha, ye, xe);
+                y[e] = fma(beta, xe, ye);
+              }
+              if (di2 < T(0x1p-64)) {  // uniform over the group
+#pragma unroll
+                for (int e = 0; e < E; ++e) x[e] *= di2;
+                di2 = ei2 = T(1);
+              }
+              if (dj2 < T(0x1p-64)) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) y[e] *= dj2;
+                dj2 = ej2 = T(1);
+              }
+#pragma unroll
+              for (int e = 0; e < E; ++e) {
+                ci[gl + G * e] = x[e];
+                cj[gl + G * e] = y[e];
+              }
+              if (gl == 0) {
+                nrm2[i] = al - t * g;
+                nrm2[j] = be + t * g;
+                dsc[i] = di2;
+                dsc[j] = dj2;
+                isc[i] = ei2;
+                isc[j] = ej2;
+                ++nrot;
+              }
+              flag = 1;
+            }
+          } else
           if (al > T(0) && be > T(0) && g * g > tol2 * al * be) {
             T cs, sn, t;
             rotation_fast(al, be, g, cs, sn, t);
@@ -457,15 +589,7 @@ jacobi_svt_kernel(const JArgs a) {
       rotated = __syncthreads_or(flag) != 0;
       ++sweeps;
     }
-    for (int c0 = 0; c0 < np; c0 += ngrp) {
-      const int c = c0 + grp;
-      const T* col = W + (size_t)ld * (c < np ? c : 0);
-      T s = T(0);
-#pragma unroll
-      for (int e = 0; e < E; ++e) s = fma(col[gl + G * e], col[gl + G * e], s);
-      s = group_sum<G>(s);
-      if (gl == 0 && c < np) nrm2[c] = s;
-    }
+    column_norms();
     if (nrot) atomicAdd(&s_rot, nrot);
     __syncthreads();
     if (a.io.phases && threadIdx.x == 0) tph[3] = clock64();
@@ -490,13 +614,13 @@ jacobi_svt_kernel(const JArgs a) {
       if (a.io.info) {
         a.io.info[slice].sweeps = sweeps;
         a.io.info[slice].rank = k;
-        a.io.info[slice].nuclear = double(nuc);
+        a.io.info[slice].nuclear = double(nuc) / double(sc);
       }
       if (a.io.flops) {
         const double md = m, nd = n;
         const double f = 2.0 * md * nd * nd - 2.0 * nd * nd * nd / 3.0 +   // QR
                          sweeps * (nd * (nd - 1) * nd + 2 * nd * nd) +      // dots + norms
-                         6.0 * nd * s_rot + 2 * nd * nd +                   // rotations
+                         (kScaled ? 4.0 : 6.0) * nd * s_rot + 2 * nd * nd + // rotations
                          4.0 * k * md * nd;                                 // reconstruction
         atomicAdd(a.io.flops, f);
       }

@@ -231,6 +231,27 @@ def test_svt_kernel_variants(prec, group, pairwise, shape):
     assert lt.lt_last_device_status(ctx) == 0
 
 
+@pytest.mark.parametrize("prec,scale", [(lt.LT_FP64, 1e-150), (lt.LT_FP64, 1e-30),
+                                        (lt.LT_FP64, 1e30), (lt.LT_FP64, 1e150),
+                                        (lt.LT_FP32, 1e-25), (lt.LT_FP32, 1e25)])
+def test_svt_is_scale_equivariant(prec, scale):
+    """D_{c tau}(c A) = c D_tau(A) (the SVT is positively homogeneous), for data far from
+    unit scale: squared norms of such slices leave the FP32 range (and, at 1e+-150, the
+    FP64 range), so this checks that the kernel keeps its arithmetic in range."""
+    rng = np.random.default_rng(77)
+    transforms = [("dct", 3)]
+    full = (40, 31, 3)
+    A = rng.standard_normal(full)
+    ref = O.svt(A, 1.5, oracle_mats(transforms)) * scale
+    ctx = make_ctx(transforms, prec)
+    dt = dtype_of(prec)
+    D = empty_dev(full, dt)
+    lt.lt_svt(ctx, to_dev(A * scale, dt), 1.5 * scale, D)
+    torch.cuda.synchronize()
+    assert rel(from_dev(D, full), ref) <= TOL[prec]
+    assert lt.lt_last_device_status(ctx) == 0
+
+
 # ------------------------------------------------------------------ PGA
 def completion_inputs(c):
     Ms = oracle_mats(c["transforms"])
