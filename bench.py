@@ -433,7 +433,7 @@ def run_case(args):
     --case product lt_product U *_L V^T of its 144x10x3x32 and 10x176x3x32 factors."""
     import torch
     from paper_2202_02870_gb300 import lt
-    prec = lt.LT_FP64 if args.precision == "fp64" else lt.LT_FP32
+    prec = {"fp64": lt.LT_FP64, "fp32": lt.LT_FP32, "mixed": lt.LT_MIXED}[args.precision]
     dt = torch.float64 if prec == lt.LT_FP64 else torch.float32
     c = problem_inputs(0)
     dev = torch.device("cuda", 0)
@@ -467,6 +467,66 @@ def run_case(args):
     print(json.dumps({"case": args.case, "precision": args.precision,
                       "jacobi_group": args.jacobi_group, "ms_per_call": ms,
                       f"{unit}_per_s": units / (ms / 1e3)}))
+
+
+def run_product5(args):
+    """--case product5: the fifth-order *_L-product 256x256x16x16x8 times
+    256x128x16x16x8 (U[-1,1]; L_k = Q_k diag(d_k), cond 1e2 each) through lt_product:
+    three transforms (modes 16, 16, 8) and the face-wise GEMM of 2048 slices of
+    (256x256)(256x128).  Reports per-call time, the per-family event times and the
+    GEMM kernel against the HBM roofline (algorithmic bytes: read A_hat and B_hat once,
+    write C_hat once) and, for LT_MIXED, the tensor-pipe rate of the three TF32
+    products it issues."""
+    import torch
+    from paper_2202_02870_gb300 import lt, synth
+    prec = {"fp64": lt.LT_FP64, "fp32": lt.LT_FP32, "mixed": lt.LT_MIXED}[args.precision]
+    dt = torch.float64 if prec == lt.LT_FP64 else torch.float32
+    c = synth.config3()
+    dev = torch.device("cuda", 0)
+    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.ravel(order="F"))).to(dt).reshape(
+        tuple(reversed(a.shape))).to(dev)
+    A, B = to_dev(c["A"]), to_dev(c["B"])
+    del c["A"], c["B"]
+    ctx = lt.Context([16, 16, 8], [np.asarray(m) for _, m in c["transforms"]], prec)
+    if args.tc_tile_n:
+        lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_TILE_N, args.tc_tile_n)
+    Cd = torch.empty((8, 16, 16, 128, 256), dtype=dt, device=dev)
+    ws = torch.empty(lt.lt_workspace_size(ctx, lt.LT_OP_PRODUCT, 256, 256, 128), dtype=torch.uint8,
+                     device=dev)
+    run = lambda: lt.lt_product(ctx, A, B, Cd, ws=ws)
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    lt.lt_ctx_get_stats(ctx, reset=True)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 1)
+    for _ in range(args.steps):
+        run()
+    st = lt.lt_ctx_get_stats(ctx, reset=True)
+    peaks = load_peaks()
+    g = st["gemm"]
+    g_ms = g["ms"] / max(g["launches"], 1)
+    gemm_bytes = g["bytes"] / max(g["launches"], 1)
+    gemm_flops = g["flops"] / max(g["launches"], 1)
+    line = {"case": "product5", "precision": args.precision, "ms_per_call": round(ms, 4),
+            "products_per_s": round(1e3 / ms, 3),
+            "kernels_ms_per_call": {k: round(st[k]["ms"] / args.steps, 4)
+                                    for k in ("transform", "gemm", "aux")},
+            "tc_launches_per_call": st["tc_launches"] / args.steps,
+            "gemm_roofline": {"bound": "hbm", "achieved": round(gemm_bytes / g_ms / 1e6, 1),
+                              "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
+                              "frac": round(gemm_bytes / g_ms / 1e6 / peaks.get("hbm_gbs", 6800.0), 4),
+                              "algorithmic_bytes": gemm_bytes, "ms_per_launch": round(g_ms, 4),
+                              "tflops_algorithmic": round(gemm_flops / g_ms / 1e9, 2)}}
+    if prec == lt.LT_MIXED:
+        line["gemm_roofline"]["tflops_issued_tf32x3"] = round(3 * gemm_flops / g_ms / 1e9, 2)
+    print(json.dumps(line))
 
 
 def run_reference(args):
@@ -513,10 +573,12 @@ def main():
                     help="timed calls of the 64-problem batch (0 skips the batched leg)")
     ap.add_argument("--batched-iters", type=int, default=4,
                     help="PGA iterations per call of the 64-problem batch")
-    ap.add_argument("--case", default="pga", choices=["pga", "svt", "product"],
+    ap.add_argument("--case", default="pga", choices=["pga", "svt", "product", "product5"],
                     help="pga: the benchmark line; svt/product: single-operation runs "
                          "used for profiling")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
+    ap.add_argument("--tc-tile-n", type=int, default=0, choices=[0, 32, 64, 128, 256],
+                    help="LT_MIXED tensor-core tile width (0: the library's choice)")
     ap.add_argument("--jacobi-group", type=int, default=0, choices=[0, 8, 16, 32],
                     help="lanes per Jacobi column pair (0: the planner's choice)")
     args = ap.parse_args()
@@ -525,6 +587,9 @@ def main():
         return
     from paper_2202_02870_gb300 import build
     build.build()
+    if args.case == "product5":
+        run_product5(args)
+        return
     if args.case != "pga":
         run_case(args)
         return

@@ -65,9 +65,13 @@ typedef enum {
 typedef enum {
   LT_FP64 = 0,  /* every step in IEEE double */
   LT_FP32 = 1,  /* every step in IEEE single (SIMT) */
-  LT_MIXED = 2  /* float data; transforms and face-wise GEMMs on the tcgen05 tensor
-                   cores as split TF32 x 3 products with FP32 accumulation; Jacobi in
-                   FP32; reductions of the PGA residual in FP64 */
+  LT_MIXED = 2  /* float data; face-wise GEMMs and the mode products of large modes
+                   (LT_OPT_TC_MODE_MIN) on the tcgen05 tensor cores as split TF32 x 3
+                   products (x = hi + lo, hi = tf32(x), lo = tf32(x - hi);
+                   hi hi + hi lo + lo hi accumulated in FP32); the other mode products,
+                   the Jacobi SVT and everything else as in LT_FP32.  Operands whose
+                   base address is not 16-byte aligned, or slices with I1 or l not a
+                   multiple of 4 (face-wise product), take the FP32 SIMT kernels. */
 } lt_precision;
 
 typedef enum {
@@ -92,9 +96,16 @@ typedef enum {
                                 stream, summed per kernel family by lt_ctx_get_stats */
   LT_OPT_JACOBI_GROUP = 4,   /* SVT kernel: lanes per column pair (8, 16 or 32); 0 (the
                                 default) lets the planner choose from min(I1, I2) */
-  LT_OPT_JACOBI_BLOCK = 5    /* SVT kernel: 1 = rotate column pairs straight through
+  LT_OPT_JACOBI_BLOCK = 5,   /* SVT kernel: 1 = rotate column pairs straight through
                                 shared memory; 0 (default) = FP32 contexts hold blocks of
                                 2-4 columns per group in registers where they fit */
+  LT_OPT_TC_MODE_MIN = 6,    /* LT_MIXED: a mode k >= 4 with I_k >= this value (default
+                                32, at most 224) is applied in a pass of its own on the
+                                tensor cores; mode 3 and smaller modes are applied by the
+                                SIMT transform kernel (fused passes); 0 = no tensor-core
+                                transform passes */
+  LT_OPT_TC_TILE_N = 7       /* LT_MIXED: output tile width of the tensor-core kernel
+                                (32, 64, 128 or 256); 0 (default) = chosen per call */
 } lt_option;
 
 /* Kernel families counted by lt_ctx_get_stats. */
@@ -119,6 +130,8 @@ typedef struct {
      split into [6] pivot search, [7] column swap, [8] Householder vector, [9] update of
      the trailing columns. */
   double jacobi_phase_cycles[10];
+  int64_t tc_launches;  /* launches of the tcgen05 tensor-core kernel (LT_MIXED), counted
+                           among the transform and GEMM launches above */
 } lt_stats;
 
 typedef struct lt_ctx_s* lt_ctx;

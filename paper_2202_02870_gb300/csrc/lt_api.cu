@@ -279,7 +279,7 @@ lt_status lt_ctx_create(int K, const int64_t* mode_sizes, const double* const* M
   if (out == nullptr) return LT_ERR_ARG;
   *out = nullptr;
   if (K < 3 || K - 2 > lt::kMaxModes || mode_sizes == nullptr || M == nullptr) return LT_ERR_ARG;
-  if (prec != LT_FP64 && prec != LT_FP32) return LT_ERR_ARG;
+  if (prec != LT_FP64 && prec != LT_FP32 && prec != LT_MIXED) return LT_ERR_ARG;
   Ctx* c = new (std::nothrow) Ctx();
   if (!c) return LT_ERR_ARG;
   c->K = K;
@@ -328,6 +328,29 @@ lt_status lt_ctx_create(int K, const int64_t* mode_sizes, const double* const* M
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, sizeof(lt::PgaScalars));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_counters, 14 * sizeof(double));
   if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, 14 * sizeof(double));
+  if (e == cudaSuccess && prec == LT_MIXED) {
+    // tensor-core B operands: B(k, n) = M(n, k) at k + n * ld, i.e. each row-major
+    // matrix with its rows padded to ld = round_up(I, 4), at 16-byte aligned offsets
+    std::vector<float> tf, ti;
+    for (int q = 0; q < c->nmodes; ++q) {
+      const int64_t n = c->sizes[q], ld = (n + 3) / 4 * 4;
+      c->tc_off[q] = (int64_t)tf.size();
+      c->tc_ld[q] = (int)ld;
+      tf.resize(tf.size() + (size_t)(n * ld), 0.0f);
+      ti.resize(ti.size() + (size_t)(n * ld), 0.0f);
+      for (int64_t r = 0; r < n; ++r)
+        for (int64_t j = 0; j < n; ++j) {
+          tf[c->tc_off[q] + r * ld + j] = (float)fwd[c->mat_off[q] + r * n + j];
+          ti[c->tc_off[q] + r * ld + j] = (float)inv[c->mat_off[q] + r * n + j];
+        }
+    }
+    e = cudaMalloc(&c->d_tc_fwd, tf.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_tc_inv, ti.size() * sizeof(float));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_tc_fwd, tf.data(), tf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_tc_inv, ti.data(), ti.size() * sizeof(float), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) { lt_ctx_destroy(reinterpret_cast<lt_ctx>(c)); return LT_ERR_CUDA; }
   *out = reinterpret_cast<lt_ctx>(c);
   return LT_OK;
@@ -342,6 +365,8 @@ lt_status lt_ctx_destroy(lt_ctx ctx) {
   if (c->d_status) cudaFree(c->d_status);
   if (c->h_pinned) cudaFreeHost(c->h_pinned);
   if (c->d_counters) cudaFree(c->d_counters);
+  if (c->d_tc_fwd) cudaFree(c->d_tc_fwd);
+  if (c->d_tc_inv) cudaFree(c->d_tc_inv);
   for (auto& r : c->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto& r : c->retired) { cudaGraphExecDestroy(r.exec); cudaEventDestroy(r.done); }
   for (auto ev : c->pool) cudaEventDestroy(ev);
@@ -374,6 +399,15 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
     case LT_OPT_JACOBI_GROUP:
       if (!(value == 0 || value == 8 || value == 16 || value == 32)) return LT_ERR_ARG;
       c->jacobi_group = (int)value;
+      return LT_OK;
+    case LT_OPT_TC_MODE_MIN:
+      if (!(value >= 0 && value <= 4096) || value != std::floor(value)) return LT_ERR_ARG;
+      c->tc_mode_min = (int)value;
+      return LT_OK;
+    case LT_OPT_TC_TILE_N:
+      if (!(value == 0 || value == 32 || value == 64 || value == 128 || value == 256))
+        return LT_ERR_ARG;
+      c->tc_tile_n = (int)value;
       return LT_OK;
   }
   return LT_ERR_ARG;
@@ -830,6 +864,8 @@ lt_status lt_ctx_get_stats(lt_ctx ctx, lt_stats* out, int reset) {
   if (e == cudaSuccess) e = cudaMemset(c->d_counters, 0, sizeof(dev));
   for (int i = 0; i < 4; ++i) c->stats.k[i].flops += dev[i];
   for (int i = 0; i < 10; ++i) c->stats.jacobi_phase_cycles[i] += dev[4 + i];
+  c->stats.tc_launches += c->tc_launches;
+  c->tc_launches = 0;
   *out = c->stats;
   if (reset) c->stats = lt_stats{};
   return cuda_status(e);

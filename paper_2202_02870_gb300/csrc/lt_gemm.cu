@@ -2,7 +2,8 @@
 // frontal slice p (the loop of Algorithm 2), all slices in one launch
 // (blockIdx.z = p).  Column-major slices: A^p is M x Kd, B^p is Kd x N, C^p is M x N.
 //
-// SIMT path (LT_FP64, LT_FP32): 64 x 64 output tile per CTA, 16-deep K steps staged in
+// SIMT path (LT_FP64, LT_FP32, and LT_MIXED slices the tensor-core kernel of
+// lt_tc_gemm.cu cannot address): 64 x 64 output tile per CTA, 16-deep K steps staged in
 // shared memory, 4 x 4 register tile per thread.
 #include "lt_internal.cuh"
 
@@ -70,6 +71,19 @@ facewise_gemm_simt(int64_t M, int64_t N, int64_t Kd, int64_t P, const T* __restr
 
 cudaError_t launch_facewise_gemm(const Ctx& c, int64_t M, int64_t N, int64_t Kd,
                                  const void* A, const void* B, void* C, cudaStream_t st) {
+  if (c.prec == LT_MIXED) {
+    // tensor cores, split TF32 x 3 (lt_tc_gemm.cu); slices whose sizes or addresses
+    // do not meet the TMA alignment rules take the FP32 SIMT kernel below
+    TcGemm g;
+    g.M = M; g.N = N; g.K = Kd; g.batch = c.P;
+    g.A = static_cast<const float*>(A); g.lda = M; g.sA = M * Kd;
+    g.B = static_cast<const float*>(B); g.ldb = Kd; g.sB = Kd * N;
+    g.D = static_cast<float*>(C); g.ldd = M; g.sD = M * N;
+    if (tc_gemm_supported(g, c.tc_tile_n)) {
+      ++c.tc_launches;
+      return launch_tc_gemm(g, c.tc_tile_n, c.d_status, st);
+    }
+  }
   const int64_t gz = c.P < 65535 ? c.P : 65535;
   dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)((N + BN - 1) / BN), (unsigned)gz);
   if (c.elem == 8)

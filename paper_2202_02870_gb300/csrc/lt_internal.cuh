@@ -37,6 +37,16 @@ struct Ctx {
   int objective = 0;
   int jacobi_group = 0;               // 0: planner's choice
   int jacobi_pairwise = 0;            // 1: no register blocking
+  int tc_mode_min = 32;               // LT_MIXED: modes of at least this size (and not
+                                      // mode 3) run as tensor-core passes; 0 = never
+  int tc_tile_n = 0;                  // LT_MIXED: forced tensor-core tile width (0 = auto)
+  mutable int64_t tc_launches = 0;    // tensor-core kernel launches (lt_ctx_get_stats)
+  // LT_MIXED: the transform matrices as tensor-core B operands, B(k, n) = M(n, k) at
+  // k + n * ld (ld = I rounded up to 4, zero padded), each at a 16-byte aligned offset.
+  float* d_tc_fwd = nullptr;
+  float* d_tc_inv = nullptr;
+  int64_t tc_off[kMaxModes] = {};
+  int tc_ld[kMaxModes] = {};
   // Pinned host staging for asynchronous reports
   void* h_pinned = nullptr;
   // Statistics (lt_ctx_get_stats)
@@ -93,6 +103,8 @@ struct TransformPass {
   int64_t Pg = 1, Sg = 1, outer = 1;
   int ts = 32;                        // tile width along Sg
   int smem = 0;                       // bytes
+  int tc = 0;                         // 1: single-mode pass on the tensor cores (LT_MIXED)
+  int tc_mode = 0;                    // its 0-based mode index
 };
 
 struct TransformPlan {
@@ -117,6 +129,28 @@ int transform_grid(const Ctx& c, const TransformPass& p);
 // ----------------------------------------------------------------------------------
 cudaError_t launch_facewise_gemm(const Ctx& c, int64_t M, int64_t N, int64_t Kd,
                                  const void* A, const void* B, void* C, cudaStream_t st);
+
+// ----------------------------------------------------------------------------------
+// Batched FP32 product on the tcgen05 tensor cores in split TF32 x 3 (lt_tc_gemm.cu):
+// D_b = A_b B_b with A_b(m,k) = A[b sA + m + k lda], B_b(k,n) = B[b sB + k + n ldb]
+// (sB = 0: shared by every b), D_b(m,n) = D[b sD + m + n ldd].  D may equal A (in
+// place) when one tile covers all N <= 256 columns.
+// ----------------------------------------------------------------------------------
+struct TcGemm {
+  int64_t M = 0, N = 0, K = 0, batch = 1;
+  const float* A = nullptr;
+  int64_t lda = 0, sA = 0;
+  const float* B = nullptr;
+  int64_t ldb = 0, sB = 0;
+  float* D = nullptr;
+  int64_t ldd = 0, sD = 0;
+};
+
+int tc_tile_n(const TcGemm& g, int forced);
+// Alignment and size conditions of the TMA descriptors (16-byte aligned A and B, lda,
+// ldb and batch strides multiples of 4 elements, sizes below 2^31).
+bool tc_gemm_supported(const TcGemm& g, int forced_bn);
+cudaError_t launch_tc_gemm(const TcGemm& g, int forced_bn, int32_t* status, cudaStream_t st);
 
 // ----------------------------------------------------------------------------------
 // Jacobi SVD / SVT (kernel J), one CTA per slice.

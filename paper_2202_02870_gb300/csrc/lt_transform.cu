@@ -251,6 +251,12 @@ lt_status plan_transform(const Ctx& c, int64_t S, bool inverse, TransformPlan* p
   const size_t budget = 200 * 1024;
   TransformPlan pl;
   pl.inverse = inverse;
+  // LT_MIXED: a large mode other than mode 3 gets a pass of its own on the tensor cores
+  // (mode 3 stays in the SIMT passes, which carry the PGA fusions).
+  auto is_tc = [&](int q) {
+    return c.prec == LT_MIXED && q >= 1 && c.tc_mode_min > 0 && c.sizes[q] >= c.tc_mode_min &&
+           c.sizes[q] <= 256;
+  };
   int k = inverse ? nm - 1 : 0;
   while (inverse ? k >= 0 : k < nm) {
     // grow the group [lo, hi] while it fits
@@ -267,8 +273,10 @@ lt_status plan_transform(const Ctx& c, int64_t S, bool inverse, TransformPlan* p
     while (ts >= 8 && !fits(lo, hi, ts)) ts /= 2;
     if (ts < 8) return LT_ERR_SHAPE;  // one mode alone too large
     for (;;) {
+      if (is_tc(k)) break;
       int nlo = inverse ? lo - 1 : lo, nhi = inverse ? hi : hi + 1;
       if (nlo < 0 || nhi >= nm) break;
+      if (is_tc(inverse ? nlo : nhi)) break;
       if (fits(nlo, nhi, 32)) { lo = nlo; hi = nhi; continue; }
       break;
     }
@@ -295,6 +303,10 @@ lt_status plan_transform(const Ctx& c, int64_t S, bool inverse, TransformPlan* p
       ps.mat_off[j] = c.mat_off[q];
     }
     ps.smem = (int)(c.elem == 8 ? smem_bytes<double>(ps, ts) : smem_bytes<float>(ps, ts));
+    if (is_tc(k)) {
+      ps.tc = 1;
+      ps.tc_mode = k;
+    }
     k = inverse ? lo - 1 : hi + 1;
   }
   *plan = pl;
@@ -314,6 +326,23 @@ cudaError_t launch_transform(const Ctx& c, const TransformPlan& plan, const void
     if (fuse) a.fuse = *fuse;
     if (fuse_mode == FUSE_PGA_FORWARD && i == 0) a.fuse_mode = FUSE_PGA_FORWARD;
     if (fuse_mode == FUSE_PGA_INVERSE && i == plan.npass - 1) a.fuse_mode = FUSE_PGA_INVERSE;
+    if (a.p.tc && a.fuse_mode == FUSE_NONE) {
+      // Y_o = X_o M_k^T for every outer block o: X_o is Sg x I column-major (Pg = I).
+      const int q = a.p.tc_mode;
+      const int64_t I = c.sizes[q];
+      TcGemm g;
+      g.M = a.p.Sg; g.N = I; g.K = I; g.batch = a.p.outer;
+      g.A = static_cast<const float*>(a.in); g.lda = a.p.Sg; g.sA = a.p.Sg * I;
+      g.B = (plan.inverse ? c.d_tc_inv : c.d_tc_fwd) + c.tc_off[q]; g.ldb = c.tc_ld[q]; g.sB = 0;
+      g.D = static_cast<float*>(out); g.ldd = a.p.Sg; g.sD = a.p.Sg * I;
+      if (tc_gemm_supported(g, c.tc_tile_n)) {
+        const cudaError_t e = launch_tc_gemm(g, c.tc_tile_n, c.d_status, st);
+        if (e != cudaSuccess) return e;
+        ++c.tc_launches;
+        continue;
+      }
+      // unaligned buffers: the SIMT kernel applies the same mode product
+    }
     const int grid = transform_grid(c, a.p);
     if (grid_out) *grid_out = grid;
     const cudaError_t e = (c.elem == 8) ? launch_pass<double>(c, a, grid, st)

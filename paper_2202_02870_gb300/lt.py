@@ -26,7 +26,7 @@ LT_DEV_NOCONV, LT_DEV_NONFINITE, LT_DEV_TIMEOUT = 1, 2, 4
 LT_FP64, LT_FP32, LT_MIXED = 0, 1, 2
 LT_OP_TRANSFORM, LT_OP_INVERSE, LT_OP_PRODUCT, LT_OP_SVD, LT_OP_SVT, LT_OP_PGA = range(6)
 (LT_OPT_MAX_SWEEPS, LT_OPT_JACOBI_TOL, LT_OPT_OBJECTIVE, LT_OPT_PROFILE, LT_OPT_JACOBI_GROUP,
- LT_OPT_JACOBI_BLOCK) = 0, 1, 2, 3, 4, 5
+ LT_OPT_JACOBI_BLOCK, LT_OPT_TC_MODE_MIN, LT_OPT_TC_TILE_N) = 0, 1, 2, 3, 4, 5, 6, 7
 LT_K_TRANSFORM, LT_K_JACOBI, LT_K_GEMM, LT_K_AUX = 0, 1, 2, 3
 KERNEL_FAMILIES = ("transform", "jacobi", "gemm", "aux")
 
@@ -51,7 +51,8 @@ class lt_kernel_stats(C.Structure):
 
 
 class lt_stats(C.Structure):
-    _fields_ = [("k", lt_kernel_stats * 4), ("jacobi_phase_cycles", C.c_double * 10)]
+    _fields_ = [("k", lt_kernel_stats * 4), ("jacobi_phase_cycles", C.c_double * 10),
+                ("tc_launches", C.c_int64)]
 
 
 SIGNATURES = {
@@ -339,6 +340,7 @@ def lt_ctx_get_stats(ctx, reset: bool = False) -> dict:
                                            "rows", "qr_pivot", "qr_swap", "qr_householder",
                                            "qr_update"),
                                           [float(v) for v in st.jacobi_phase_cycles]))
+    out["tc_launches"] = int(st.tc_launches)
     return out
 
 
