@@ -11,8 +11,9 @@ value     PGA iterations per second of the plain FP64 path, summed over ranks, i
           resident in HBM.  L2 is flushed (a 512 MiB write) between timed steps.
 e2e       the same metric through the C ABI with host buffers: the pinned-host mask and
           observations are copied in and the result copied out inside every step.
-mixed     the FP32 path on the same inputs, with its relative error against the FP64
-          result of the same run.
+mixed     the LT_MIXED path on the same inputs (FP32 data; the mode-32 products on the
+          tcgen05 tensor cores in split TF32 x 3), with its relative error against
+          the FP64 result of the same run; fp32: the same for the all-SIMT FP32 path.
 roofline  the Jacobi SVT kernel (dominant): executed-flop count reported by the kernel
           / its CUDA-event time over the timed steps, against the FP64 FMA peak measured
           on this GPU (ALU-bound: the FP64 pipe).
@@ -259,16 +260,31 @@ def run_ours(args):
     gpu_launches = st64["timed_launches"]  # launches of the K timed steps
     slices_per_s = 96 / (jac_ms_avg / 1e3) if jac_ms_avg > 0 else 0.0
 
-    # ---------------- FP32 path on the same inputs
-    ctx32 = ctx_for(lt.LT_FP32)
-    X32, ms32, _, st32, rep32 = run_path(ctx32, obs32, torch.float32, args.steps, args.warmup, True)
-    mixed_ms = statistics.mean(ms32)
-    rel32 = float(torch.linalg.norm(X32.double() - X64) / torch.linalg.norm(X64))
-    j32 = st32["jacobi"]
-    j32_ms = j32["ms"] / max(j32["launches"], 1)
+    # ---------------- FP32 and mixed (LT_MIXED: tensor-core mode-32 passes) paths on the
+    # same inputs
+    def single_leg(prec, label):
+        ctxp = ctx_for(prec)
+        Xp, msp, _, stp, _ = run_path(ctxp, obs32, torch.float32, args.steps, args.warmup, True)
+        mean_ms = statistics.mean(msp)
+        relp = float(torch.linalg.norm(Xp.double() - X64) / torch.linalg.norm(X64))
+        jp = stp["jacobi"]
+        jp_ms = jp["ms"] / max(jp["launches"], 1)
+        jp_flops = jp["flops"] / max(jp["launches"], 1)
+        jp_ach = jp_flops / (jp_ms / 1e3) / 1e9 if jp_ms > 0 else 0.0
+        tr = stp["transform"]
+        return {"dtype": label, "value": round(ws * iters / (mean_ms / 1e3), 3),
+                "unit": "iters/s", "ms_per_step": round(mean_ms, 3),
+                "rel_err_vs_fp64": relp,
+                "svt_slices_per_s": round(96 / (jp_ms / 1e3), 1) if jp_ms > 0 else None,
+                "transform_ms_per_step": round(tr["ms"] / args.steps, 3),
+                "tc_launches_per_step": stp["tc_launches"] / args.steps,
+                "roofline": {"kernel": "jacobi_svt (FP32)", "bound": "alu",
+                             "achieved": round(jp_ach, 1), "peak": FP32_PEAK_GFLOPS,
+                             "unit": "GFLOP/s", "frac": round(jp_ach / FP32_PEAK_GFLOPS, 4),
+                             "peak_source": "measured FP32 FMA throughput (of measured)"}}
 
-    j32_flops = j32["flops"] / max(j32["launches"], 1)
-    j32_achieved = j32_flops / (j32_ms / 1e3) / 1e9 if j32_ms > 0 else 0.0
+    fp32_leg = single_leg(lt.LT_FP32, "f32")
+    mixed_leg = single_leg(lt.LT_MIXED, "f32 + split-tf32x3 tensor cores")
 
     # ---------------- batched: the 64 uneven problems of one batch, FP32
     batched = None
@@ -340,14 +356,8 @@ def run_ours(args):
                        "l2": "flushed between steps (512 MiB write)",
                        "parallelism": f"replicas x{ws}"},
             "svt_slices_per_s": round(slices_per_s, 1),
-            "mixed": {"dtype": "f32", "value": round(ws * iters / (mixed_ms / 1e3), 3),
-                      "unit": "iters/s", "ms_per_step": round(mixed_ms, 3),
-                      "rel_err_vs_fp64": rel32,
-                      "svt_slices_per_s": round(96 / (j32_ms / 1e3), 1) if j32_ms > 0 else None,
-                      "roofline": {"kernel": "jacobi_svt (FP32)", "bound": "alu",
-                                   "achieved": round(j32_achieved, 1), "peak": FP32_PEAK_GFLOPS,
-                                   "unit": "GFLOP/s", "frac": round(j32_achieved / FP32_PEAK_GFLOPS, 4),
-                                   "peak_source": "measured FP32 FMA throughput (of measured)"}},
+            "mixed": mixed_leg,
+            "fp32": fp32_leg,
             "batched": batched,
             "roofline": {"kernel": "jacobi_svt (FP64)", "bound": "alu",
                          "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
@@ -379,7 +389,7 @@ def run_ours(args):
 
 def run_batched_leg(args, dev, ws):
     """The 64 independent completion problems of uneven sizes (I1 x I2 from 64 x 48 to
-    512 x 384, I3 = 3, I4 in {8, 16, 32, 64}, DCT transforms), FP32: one
+    512 x 384, I3 = 3, I4 in {8, 16, 32, 64}, DCT transforms), LT_MIXED: one
     lt_pga_complete_batched call (a CUDA graph with a branch per problem) of `iters`
     iterations per step, against the same problems issued one after the other."""
     import torch
@@ -392,7 +402,7 @@ def run_batched_leg(args, dev, ws):
         full = (sh["I1"], sh["I2"]) + sh["trailing"]
         elems += int(np.prod(full))
         ctxs.append(lt.Context(list(sh["trailing"]), [lt.lt_make_dct(n) for n in sh["trailing"]],
-                               lt.LT_FP32))
+                               lt.LT_MIXED))
         m = torch.from_numpy((rng.random(int(np.prod(full))) < sh["rho"]).astype(np.uint8))
         masks.append(m.reshape(tuple(reversed(full))).to(dev))
         obss.append(masks[-1].float() * torch.randn(tuple(reversed(full)), device=dev))
@@ -420,7 +430,8 @@ def run_batched_leg(args, dev, ws):
     e1.record(st)
     torch.cuda.synchronize()
     ms_s = e0.elapsed_time(e1)
-    return {"problems": n, "elements": elems, "iters_per_step": iters, "dtype": "f32",
+    return {"problems": n, "elements": elems, "iters_per_step": iters,
+            "dtype": "f32 + split-tf32x3 tensor cores",
             "value": round(ws * n * iters / (ms_b / 1e3), 2), "unit": "problem-iters/s",
             "ms_per_step": round(ms_b, 2), "sequential_ms": round(ms_s, 2),
             "speedup_vs_sequential": round(ms_s / ms_b, 3)}
