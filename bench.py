@@ -540,6 +540,51 @@ def run_product5(args):
     print(json.dumps(line))
 
 
+def run_transform5(args):
+    """--case transform5: lt_transform + lt_inverse of a 540x960x3x120 tensor (the large
+    completion's shape; L_3 = DCT 3, L_4 = Q1 diag(d) Q2^T with cond 10), U[-1,1].
+    Reports per-call times and the transform kernels against HBM (one read and one
+    write of the tensor per pass) and the FP32 FMA rate."""
+    import torch
+    from paper_2202_02870_gb300 import lt, synth
+    prec = {"fp64": lt.LT_FP64, "fp32": lt.LT_FP32, "mixed": lt.LT_MIXED}[args.precision]
+    dt = torch.float64 if prec == lt.LT_FP64 else torch.float32
+    rng = synth.rng_for(5, 1)
+    M4 = synth.conditioned_matrix(rng, 120, 10.0, two_sided=True)
+    ctx = lt.Context([3, 120], [lt.lt_make_dct(3), M4], prec)
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(20220706)
+    X = (torch.rand((120, 3, 960, 540), generator=g, device=dev, dtype=torch.float32) * 2 - 1).to(dt)
+    Xh = torch.empty_like(X)
+    run = lambda: (lt.lt_transform(ctx, X, Xh), lt.lt_inverse(ctx, Xh, Xh))
+    for _ in range(args.warmup):
+        run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    lt.lt_ctx_get_stats(ctx, reset=True)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 1)
+    for _ in range(args.steps):
+        run()
+    st = lt.lt_ctx_get_stats(ctx, reset=True)
+    tr = st["transform"]
+    peaks = load_peaks()
+    print(json.dumps({"case": "transform5", "precision": args.precision,
+                      "ms_per_transform_and_inverse": round(ms, 4),
+                      "transform_kernel_ms": round(tr["ms"] / args.steps, 4),
+                      "launches_per_call": tr["launches"] / args.steps,
+                      "tc_launches_per_call": st["tc_launches"] / args.steps,
+                      "gflops_algorithmic": round(tr["flops"] / max(tr["ms"], 1e-9) / 1e6, 1),
+                      "hbm_gbs_algorithmic": round(tr["bytes"] / max(tr["ms"], 1e-9) / 1e6, 1),
+                      "hbm_peak_gbs": peaks.get("hbm_gbs")}))
+
+
 def run_reference(args):
     """The FP64 oracle as it stands, on the host cores: each step is a bounded sample of
     the same workload (ORACLE_ITERS_PER_STEP PGA iterations)."""
@@ -584,7 +629,8 @@ def main():
                     help="timed calls of the 64-problem batch (0 skips the batched leg)")
     ap.add_argument("--batched-iters", type=int, default=4,
                     help="PGA iterations per call of the 64-problem batch")
-    ap.add_argument("--case", default="pga", choices=["pga", "svt", "product", "product5"],
+    ap.add_argument("--case", default="pga",
+                    choices=["pga", "svt", "product", "product5", "transform5"],
                     help="pga: the benchmark line; svt/product: single-operation runs "
                          "used for profiling")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
@@ -600,6 +646,9 @@ def main():
     build.build()
     if args.case == "product5":
         run_product5(args)
+        return
+    if args.case == "transform5":
+        run_transform5(args)
         return
     if args.case != "pga":
         run_case(args)

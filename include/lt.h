@@ -100,10 +100,10 @@ typedef enum {
                                 shared memory; 0 (default) = FP32 contexts hold blocks of
                                 2-4 columns per group in registers where they fit */
   LT_OPT_TC_MODE_MIN = 6,    /* LT_MIXED: a mode k >= 4 with I_k >= this value (default
-                                32, at most 224) is applied in a pass of its own on the
-                                tensor cores; mode 3 and smaller modes are applied by the
-                                SIMT transform kernel (fused passes); 0 = no tensor-core
-                                transform passes */
+                                64; modes above 224 never) is applied in a pass of its own
+                                on the tensor cores; mode 3 and smaller modes are applied
+                                by the SIMT transform kernel (fused passes); 0 = no
+                                tensor-core transform passes */
   LT_OPT_TC_TILE_N = 7       /* LT_MIXED: output tile width of the tensor-core kernel
                                 (32, 64, 128 or 256); 0 (default) = chosen per call */
 } lt_option;

@@ -37,7 +37,7 @@ struct Ctx {
   int objective = 0;
   int jacobi_group = 0;               // 0: planner's choice
   int jacobi_pairwise = 0;            // 1: no register blocking
-  int tc_mode_min = 32;               // LT_MIXED: modes of at least this size (and not
+  int tc_mode_min = 64;               // LT_MIXED: modes of at least this size (and not
                                       // mode 3) run as tensor-core passes; 0 = never
   int tc_tile_n = 0;                  // LT_MIXED: forced tensor-core tile width (0 = auto)
   mutable int64_t tc_launches = 0;    // tensor-core kernel launches (lt_ctx_get_stats)

@@ -23,7 +23,10 @@ namespace lt {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kR = 4;  // outputs per work item (register blocking along the mode)
+constexpr int kR = 4;  // FP64: outputs per work item (register blocking along the mode)
+
+// FP32 coefficient rows are padded to a multiple of 8 (two 16-byte loads per row chunk).
+__host__ __device__ constexpr int padded_rows(int I) { return (I + 7) / 8 * 8; }
 
 template <typename T>
 struct Acc;  // per-tile accumulator type of the epilogue sums
@@ -59,16 +62,27 @@ transform_kernel(const PassArgs a) {
   T* buf1 = buf0 + (size_t)Pg * TS;
   T* mats_s = buf1 + (size_t)Pg * TS;
 
-  // Stage the pass's matrices (row-major I x I each) in shared memory.
+  // Stage the pass's matrices in shared memory: FP64 row-major I x I; FP32 transposed
+  // with rows padded to a multiple of 8 (MT[i][j] = M[j][i], zeros beyond I), so that
+  // eight consecutive outputs read their coefficients with two 16-byte loads.
   int moff_s[kMaxModes];
   {
     int acc = 0;
     for (int q = 0; q < p.nm; ++q) {
       moff_s[q] = acc;
       const T* src = reinterpret_cast<const T*>(a.mats) + p.mat_off[q];
-      const int cnt = p.msize[q] * p.msize[q];
-      for (int i = threadIdx.x; i < cnt; i += blockDim.x) mats_s[acc + i] = src[i];
-      acc += cnt;
+      const int I = p.msize[q];
+      if constexpr (sizeof(T) == 4) {
+        const int Ip = padded_rows(I);
+        for (int idx = threadIdx.x; idx < I * Ip; idx += blockDim.x) {
+          const int i = idx / Ip, j = idx % Ip;
+          mats_s[acc + idx] = j < I ? src[j * I + i] : T(0);
+        }
+        acc += I * Ip;
+      } else {
+        for (int idx = threadIdx.x; idx < I * I; idx += blockDim.x) mats_s[acc + idx] = src[idx];
+        acc += I * I;
+      }
     }
   }
   __syncthreads();
@@ -118,6 +132,53 @@ transform_kernel(const PassArgs a) {
     // ---- mode products, one mode after the other
     T* src = buf0;
     T* dst = buf1;
+    if constexpr (sizeof(T) == 4) {
+      // FP32: a work item is (fiber, 8 consecutive outputs j0..j0+7, 4 consecutive
+      // columns); per input index i one 16-byte load of x (4 columns) and two of the
+      // coefficients feed 32 FMAs.  Items are ordered output chunk first, so the 8 x 4
+      // threads of a warp mostly share j0 (uniform coefficient loads).
+      constexpr int R = 8, C = 4;
+      const int cg = threadIdx.x % (TS / C);
+      const int rs = threadIdx.x / (TS / C);
+      const int nrs = blockDim.x / (TS / C);
+      for (int q = 0; q < p.nm; ++q) {
+        const int I = p.msize[q], st = p.mstride[q], Ip = padded_rows(I);
+        const T* MT = mats_s + moff_s[q];
+        const int nch = (I + R - 1) / R, nfib = Pg / I;
+        const int items = nch * nfib;
+        for (int it = rs; it < items; it += nrs) {
+          const int ch = it / nfib, fiber = it % nfib;
+          const int aa = fiber % st, bb = fiber / st;
+          const int fbase = aa + st * I * bb;
+          const int j0 = ch * R;
+          float acc[R][C];
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[r][c] = 0.f;
+          const float* xp = src + (size_t)fbase * TS + cg * C;
+          const float* mp = MT + j0;
+          for (int i = 0; i < I; ++i) {
+            const float4 x = *reinterpret_cast<const float4*>(xp + (size_t)st * i * TS);
+            const float4 m0 = *reinterpret_cast<const float4*>(mp + i * Ip);
+            const float4 m1 = *reinterpret_cast<const float4*>(mp + i * Ip + 4);
+            const float mv[R] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+            const float xv[C] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+#pragma unroll
+              for (int c = 0; c < C; ++c) acc[r][c] = fmaf(mv[r], xv[c], acc[r][c]);
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+            if (j0 + r < I)
+              *reinterpret_cast<float4*>(dst + (size_t)(fbase + st * (j0 + r)) * TS + cg * C) =
+                  make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+        }
+        __syncthreads();
+        T* t = src; src = dst; dst = t;
+      }
+    } else
     for (int q = 0; q < p.nm; ++q) {
       const int I = p.msize[q], st = p.mstride[q];
       const T* M = mats_s + moff_s[q];
@@ -193,7 +254,8 @@ transform_kernel(const PassArgs a) {
 template <typename T>
 size_t smem_bytes(const TransformPass& p, int ts) {
   size_t mats = 0;
-  for (int q = 0; q < p.nm; ++q) mats += (size_t)p.msize[q] * p.msize[q];
+  for (int q = 0; q < p.nm; ++q)
+    mats += (size_t)p.msize[q] * (sizeof(T) == 4 ? padded_rows(p.msize[q]) : p.msize[q]);
   return (2 * (size_t)p.Pg * ts + mats) * sizeof(T);
 }
 
@@ -208,6 +270,10 @@ cudaError_t launch_pass_t(const Ctx& c, const PassArgs& a, int grid, cudaStream_
 
 template <typename T>
 cudaError_t launch_pass(const Ctx& c, const PassArgs& a, int grid, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {  // wide tiles for passes over few, short fibres
+    if (a.p.ts == 512) return launch_pass_t<T, 512>(c, a, grid, st);
+    if (a.p.ts == 128) return launch_pass_t<T, 128>(c, a, grid, st);
+  }
   switch (a.p.ts) {
     case 32: return launch_pass_t<T, 32>(c, a, grid, st);
     case 16: return launch_pass_t<T, 16>(c, a, grid, st);
@@ -227,6 +293,10 @@ int occupancy(const TransformPass& p) {
 
 template <typename T>
 int occupancy_t(const TransformPass& p) {
+  if constexpr (sizeof(T) == 4) {
+    if (p.ts == 512) return occupancy<T, 512>(p);
+    if (p.ts == 128) return occupancy<T, 128>(p);
+  }
   switch (p.ts) {
     case 32: return occupancy<T, 32>(p);
     case 16: return occupancy<T, 16>(p);
@@ -248,7 +318,9 @@ lt_status plan_transform(const Ctx& c, int64_t S, bool inverse, TransformPlan* p
   // 0-based modes; for the inverse the ranges are visited from the last mode down and
   // each pass applies its modes from its highest to its lowest.
   const int nm = c.nmodes;
-  const size_t budget = 200 * 1024;
+  // FP64 passes are bound by the FP64 pipe: fewest passes.  FP32 passes keep two CTAs
+  // per SM (loads of one tile overlap the mode products of the other).
+  const size_t budget = c.elem == 8 ? 200 * 1024 : 110 * 1024;
   TransformPlan pl;
   pl.inverse = inverse;
   // LT_MIXED: a large mode other than mode 3 gets a pass of its own on the tensor cores
@@ -280,9 +352,24 @@ lt_status plan_transform(const Ctx& c, int64_t S, bool inverse, TransformPlan* p
       if (fits(nlo, nhi, 32)) { lo = nlo; hi = nhi; continue; }
       break;
     }
-    // TS: widest that fits
+    // TS: widest that fits; FP32 passes over few rows (Pg small) take wider tiles (up to
+    // 8192 elements) while that still leaves two tiles per SM
     ts = 32;
     while (ts > 8 && !fits(lo, hi, ts)) ts /= 2;
+    if (c.elem == 4 && ts == 32) {
+      int64_t pg = 1, before = 1;
+      for (int q = lo; q <= hi; ++q) pg *= c.sizes[q];
+      for (int q = 0; q < lo; ++q) before *= c.sizes[q];
+      int64_t outer = 1;
+      for (int q = hi + 1; q < nm; ++q) outer *= c.sizes[q];
+      const int64_t sg = S * before;
+      for (int w : {512, 128}) {
+        if (pg * w <= 8192 && fits(lo, hi, w) && outer * ((sg + w - 1) / w) >= 2 * (int64_t)c.sms) {
+          ts = w;
+          break;
+        }
+      }
+    }
     TransformPass& ps = pl.pass[pl.npass++];
     ps.nm = hi - lo + 1;
     ps.ts = ts;

@@ -135,6 +135,7 @@ def test_mixed_transform_and_inverse(shape, transforms, ntc):
     X = rng.uniform(-1, 1, size=full)
     Ms = oracle_mats(transforms)
     ctx = make_ctx(transforms, MIXED)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_MODE_MIN, 32)
     Xd = to_dev(X, torch.float32)
     Xh = empty_dev(full, torch.float32)
     lt.lt_transform(ctx, Xd, Xh)
@@ -154,16 +155,17 @@ def test_mixed_transform_and_inverse(shape, transforms, ntc):
 
 
 def test_mixed_tc_mode_min_option_routes_passes():
-    """LT_OPT_TC_MODE_MIN = 0 keeps every mode product in the SIMT kernel; the results
-    agree with the tensor-core route to the bound."""
+    """LT_OPT_TC_MODE_MIN routes the mode-32 products (0: never on the tensor cores; 32:
+    on them; 33 and the default 64: not); the results agree to the bound."""
     rng = np.random.default_rng(3)
     X = rng.uniform(-1, 1, (8, 6, 3, 32))
     tr = [("dct", 3), ("dct", 32)]
     Ms = oracle_mats(tr)
     ref = O.transform(X, Ms)
-    for mode_min, ntc in ((0, 0), (32, 1), (33, 0)):
+    for mode_min, ntc in ((0, 0), (32, 1), (33, 0), (None, 0)):
         ctx = make_ctx(tr, MIXED)
-        lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_MODE_MIN, mode_min)
+        if mode_min is not None:  # None: the default (64) keeps mode 32 in the SIMT pass
+            lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_MODE_MIN, mode_min)
         Xh = empty_dev(X.shape, torch.float32)
         lt.lt_transform(ctx, to_dev(X, torch.float32), Xh)
         torch.cuda.synchronize()
@@ -172,8 +174,9 @@ def test_mixed_tc_mode_min_option_routes_passes():
 
 
 def test_mixed_pga_small():
-    """PGA (Algorithm 5) on a 24 x 20 x 3 x 32 completion problem in LT_MIXED: the mode-4
-    products run on the tensor cores inside every iteration."""
+    """PGA (Algorithm 5) on a 24 x 20 x 3 x 32 completion problem in LT_MIXED with the
+    mode-4 products routed to the tensor cores (LT_OPT_TC_MODE_MIN = 32) inside every
+    iteration."""
     c = synth.completion_case(11, 24, 20, (3, 32), rank=3, rho=0.4)
     tr = [("dct", 3), ("dct", 32)]
     Ms = oracle_mats(tr)
@@ -181,6 +184,7 @@ def test_mixed_pga_small():
     obs = c["mask"] * (X0 + c["noise"])
     ref, _ = O.pga(c["mask"], obs, 0.3, 1.0, 20, Ms)
     ctx = make_ctx(tr, MIXED)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_MODE_MIN, 32)
     X = torch.zeros((32, 3, 20, 24), dtype=torch.float32, device="cuda")
     rep = lt.lt_pga_report()
     lt.lt_pga_complete(ctx, to_dev(c["mask"]), to_dev(obs, torch.float32), 0.3, 1.0, 20, X,
