@@ -18,22 +18,27 @@
 // B_b(k, n) = B[b sB + k + n ldb] (K contiguous; sB = 0 when every block shares B),
 // D_b(m, n) = D[b sD + m + n ldd].
 //
-// One CTA computes one 128 x BN tile of one D_b, K in chunks of 32:
-//   warp 4    TMA producer (one thread): per chunk, the raw A chunk (128 x 32, M
+// Persistent kernel, one CTA per SM; a CTA takes 128 x BN output tiles of the D_b in
+// turn (column tiles fastest), K in chunks of 32 FP32 (one 128-byte row):
+//   warp 8    TMA producer (one thread): per chunk, the raw A chunk (128 x 32, M
 //             fastest, no swizzle) and the B chunk (32 x BN, K fastest, 128-byte swizzle,
-//             which is the K-major canonical operand layout) into a ring of stages,
-//             completion counted on an mbarrier (complete_tx).
-//   warps 0-3 converters: split the A chunk into hi and lo and write both transposed
-//             into the K-major 128-byte-swizzled operand layout (the raw A buffer is
-//             reused for lo); split B in place (hi) and into a lo buffer.  Then the
-//             epilogue: TMEM -> registers (tcgen05.ld, one accumulator row per thread)
-//             -> global, 32 consecutive rows per warp store.
-//   warp 5    TMEM allocation and the MMA issuer (one thread): per 8-deep K step three
-//             tcgen05.mma kind::tf32 into one 128 x BN FP32 accumulator in TMEM;
-//             tcgen05.commit releases a stage and finally signals the epilogue.
+//             which is the K-major canonical operand layout) into a ring of up to six
+//             raw stages, completion counted on an mbarrier (complete_tx).
+//   warps 4-7 converters (one accumulator row per thread): read a raw stage into
+//             registers and release it at once, then write hi and lo of A transposed
+//             into the K-major 128-byte-swizzled layout and hi and lo of B at the raw
+//             (swizzled) positions into a ring of two converted stages.
+//   warp 9    TMEM allocation (two accumulators of BN columns) and the MMA issuer (one
+//             thread): per 8-deep K step three tcgen05.mma kind::tf32 (hi hi, hi lo,
+//             lo hi) into the 128 x BN FP32 accumulator of the tile; tcgen05.commit
+//             releases a converted stage and, after the last chunk, hands the
+//             accumulator to the epilogue.
+//   warps 0-3 epilogue: TMEM -> registers (tcgen05.ld, one row per thread) -> global
+//             (32 consecutive rows per warp store) while the next tile accumulates in
+//             the other accumulator.
 // Every wait on an mbarrier is bounded (1 s): on expiry the CTA raises LT_DEV_TIMEOUT,
-// stops issuing work, waits (bounded) for its own copies and MMAs in flight, frees its
-// TMEM and returns.
+// every role stops issuing work, the producer waits (bounded) for its copies in flight,
+// the issuer for its MMAs, the TMEM is freed and the CTA returns.
 #include <cuda.h>
 
 #include <mutex>
@@ -45,19 +50,21 @@ namespace {
 
 constexpr int kBM = 128;                      // tile rows (TMEM lanes)
 constexpr int kBK = 32;                       // K per chunk: one 128-byte row of FP32
-constexpr int kThreads = 192;                 // warps 0-3 convert, 4 loads, 5 issues
-constexpr int kMaxStages = 4;
+constexpr int kThreads = 320;                 // warps 0-3 epilogue, 4-7 convert, 8 loads,
+                                              // 9 allocates TMEM and issues the MMAs
+constexpr int kMaxRaw = 6;                    // raw (TMA) stages at most
 constexpr uint32_t kABytes = kBM * kBK * 4;   // 16 KiB per A buffer
+constexpr int kSmemLimit = 232448;            // opt-in shared memory per block
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 struct TcParams {
-  int64_t M, N, K;
+  int64_t M, N, K, batch;
   float* D;
   int64_t ldd, sD;
   int64_t m_tiles, n_tiles;
-  int stages;
+  int raw_stages;       // TMA ring depth (<= kMaxRaw)
+  int conv_stages;      // converted-operand ring depth (1 or 2)
   int b_batched;        // B has a batch coordinate (else every block uses B_0)
-  uint32_t stage_bytes;
   int32_t* status;      // device status word (LT_DEV_TIMEOUT)
 };
 
@@ -134,10 +141,6 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-__device__ __forceinline__ void converters_sync() {  // named barrier of warps 0-3
-  asm volatile("bar.sync 1, 128;" ::: "memory");
-}
-
 // Shared-memory operand descriptor of a K-major tile in the 128-byte swizzled canonical
 // layout: rows of 128 bytes (32 FP32 along K), groups of 8 rows 1024 bytes apart,
 // 1024-byte aligned groups.  Fields: start address >> 4 (bits 0-13), leading byte
@@ -197,44 +200,53 @@ template <int BN>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
                const __grid_constant__ CUtensorMap map_b, const TcParams p) {
-  constexpr uint32_t kBBytes = BN * 128;   // one B buffer: BN rows of 128 bytes
-  constexpr uint32_t kTmemCols = BN < 32 ? 32 : BN;
+  constexpr uint32_t kBBytes = BN * 128;                  // one B buffer: BN rows of 128 B
+  constexpr uint32_t kRawBytes = kABytes + kBBytes;       // raw A [k][m] + raw B (swizzled)
+  constexpr uint32_t kConvBytes = 2 * kABytes + 2 * kBBytes;  // A hi, A lo, B hi, B lo
+  constexpr uint32_t kAccCols = BN < 32 ? 32 : BN;
+  constexpr uint32_t kTmemCols = 2 * kAccCols;            // two accumulators
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
-  const uint32_t base = (raw_addr + 1023u) & ~1023u;  // swizzled tiles: 1024-aligned
+  const uint32_t base = (raw_addr + 1023u) & ~1023u;      // swizzled tiles: 1024-aligned
   unsigned char* sbase = smem_raw + (base - raw_addr);
-  const int S = p.stages;
-  const uint32_t SB = p.stage_bytes;
-  // control block after the stages: full[4] conv[4] empty[4] acc | tmem address | abort
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + (size_t)S * SB);
-  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 13);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(bars + 14);
+  const int R = p.raw_stages, C = p.conv_stages;
+  const uint32_t conv0 = (uint32_t)R * kRawBytes;         // conv ring after the raw ring
+  // control block: raw_full[6] raw_empty[6] conv_full[2] conv_empty[2] acc_full[2]
+  // acc_empty[2] done | tmem address | abort
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + conv0 + (size_t)C * kConvBytes);
+  uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(bars + 2 * kMaxRaw + 4 * 2 + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
   const uint32_t bar0 = smem_u32(bars);
-  auto full_bar = [&](int s) { return bar0 + 8u * s; };
-  auto conv_bar = [&](int s) { return bar0 + 8u * (kMaxStages + s); };
-  auto empty_bar = [&](int s) { return bar0 + 8u * (2 * kMaxStages + s); };
-  const uint32_t acc_bar = bar0 + 8u * 3 * kMaxStages;
+  auto raw_full = [&](int i) { return bar0 + 8u * i; };
+  auto raw_empty = [&](int i) { return bar0 + 8u * (kMaxRaw + i); };
+  auto conv_full = [&](int i) { return bar0 + 8u * (2 * kMaxRaw + i); };
+  auto conv_empty = [&](int i) { return bar0 + 8u * (2 * kMaxRaw + 2 + i); };
+  auto acc_full = [&](int i) { return bar0 + 8u * (2 * kMaxRaw + 4 + i); };
+  auto acc_empty = [&](int i) { return bar0 + 8u * (2 * kMaxRaw + 6 + i); };
+  const uint32_t done_bar = bar0 + 8u * (2 * kMaxRaw + 8);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t tile = blockIdx.x;
-  const int64_t nt = tile % p.n_tiles;
-  const int64_t rest = tile / p.n_tiles;
-  const int64_t mt = rest % p.m_tiles;
-  const int64_t b = rest / p.m_tiles;
-  const int m0 = (int)(mt * kBM), n0 = (int)(nt * BN);
   const int nchunks = (int)((p.K + kBK - 1) / kBK);
+  const int64_t ntiles = p.batch * p.m_tiles * p.n_tiles;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(full_bar(s), 1);
-      mbar_init(conv_bar(s), 128);
-      mbar_init(empty_bar(s), 1);
+    for (int i = 0; i < R; ++i) {
+      mbar_init(raw_full(i), 1);
+      mbar_init(raw_empty(i), 128);
     }
-    mbar_init(acc_bar, 1);
+    for (int i = 0; i < C; ++i) {
+      mbar_init(conv_full(i), 128);
+      mbar_init(conv_empty(i), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(acc_full(i), 1);
+      mbar_init(acc_empty(i), 128);
+    }
+    mbar_init(done_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 5) {
+  if (warp == 9) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_holder)),
                  "r"(kTmemCols)
@@ -246,74 +258,118 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
-  if (warp == 4) {
+  // tile t -> (batch b, row tile, column tile), column tiles fastest (neighbouring CTAs
+  // share the A tile in L2)
+  auto tile_coords = [&](int64_t t, int64_t& b, int& m0, int& n0) {
+    const int64_t nt = t % p.n_tiles;
+    const int64_t rest = t / p.n_tiles;
+    m0 = (int)((rest % p.m_tiles) * kBM);
+    b = rest / p.m_tiles;
+    n0 = (int)(nt * BN);
+  };
+
+  if (warp == 8) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
-      int last[kMaxStages];
-      for (int s = 0; s < kMaxStages; ++s) last[s] = -1;
-      for (int c = 0; c < nchunks; ++c) {
-        const int s = c % S;
-        if (c >= S && !mbar_wait(empty_bar(s), (uint32_t)((c / S) - 1) & 1u, abort_flag,
-                                 p.status, true))
-          break;
-        const uint32_t st = base + (uint32_t)s * SB;
-        mbar_expect_tx(full_bar(s), kABytes + kBBytes);
-        tma_load_3d(st, &map_a, full_bar(s), m0, c * kBK, (int)b);
-        tma_load_3d(st + 2 * kABytes, &map_b, full_bar(s), c * kBK, n0, p.b_batched ? (int)b : 0);
-        last[s] = c;
+      int last[kMaxRaw];
+      for (int i = 0; i < kMaxRaw; ++i) last[i] = -1;
+      int64_t g = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
+        int64_t b;
+        int m0, n0;
+        tile_coords(t, b, m0, n0);
+        for (int c = 0; c < nchunks; ++c, ++g) {
+          const int r = (int)(g % R);
+          if (g >= R && !mbar_wait(raw_empty(r), (uint32_t)((g / R) - 1) & 1u, abort_flag,
+                                   p.status, true)) {
+            ok = false;
+            break;
+          }
+          const uint32_t st = base + (uint32_t)r * kRawBytes;
+          mbar_expect_tx(raw_full(r), kRawBytes);
+          tma_load_3d(st, &map_a, raw_full(r), m0, c * kBK, (int)b);
+          tma_load_3d(st + kABytes, &map_b, raw_full(r), c * kBK, n0, p.b_batched ? (int)b : 0);
+          last[r] = (int)(g / R);
+        }
       }
-      // Never leave while copies into this CTA's shared memory are in flight.
-      for (int s = 0; s < S; ++s)
-        if (last[s] >= 0)
-          mbar_wait(full_bar(s), (uint32_t)(last[s] / S) & 1u, abort_flag, p.status, false);
+      // never leave while copies into this CTA's shared memory are in flight
+      for (int i = 0; i < R; ++i)
+        if (last[i] >= 0) mbar_wait(raw_full(i), (uint32_t)last[i] & 1u, abort_flag, p.status, false);
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       // instruction descriptor: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 =
       // 2), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28
       const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) |
                              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
-      for (int c = 0; c < nchunks; ++c) {
-        const int s = c % S;
-        if (!mbar_wait(conv_bar(s), (uint32_t)(c / S) & 1u, abort_flag, p.status, true)) break;
+      int64_t g = 0, it = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++it) {
+        const int a = (int)(it & 1);
+        if (it >= 2 && !mbar_wait(acc_empty(a), (uint32_t)((it / 2) - 1) & 1u, abort_flag,
+                                  p.status, true))
+          break;
         tc_fence_after();
-        const uint32_t st = base + (uint32_t)s * SB;
-        const uint32_t a_lo = st, a_hi = st + kABytes;
-        const uint32_t b_hi = st + 2 * kABytes, b_lo = b_hi + kBBytes;
+        const uint32_t dacc = tmem + (uint32_t)a * kAccCols;
+        for (int c = 0; c < nchunks; ++c, ++g) {
+          const int q = (int)(g % C);
+          if (!mbar_wait(conv_full(q), (uint32_t)(g / C) & 1u, abort_flag, p.status, true)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = base + conv0 + (uint32_t)q * kConvBytes;
+          const uint32_t a_hi = st, a_lo = st + kABytes;
+          const uint32_t b_hi = st + 2 * kABytes, b_lo = b_hi + kBBytes;
 #pragma unroll
-        for (int ks = 0; ks < kBK / 8; ++ks) {  // 8 TF32 = 32 bytes per MMA
-          const uint32_t off = 32u * ks;
-          mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc,
-                   (c > 0 || ks > 0) ? 1u : 0u);
-          mma_tf32(tmem, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
-          mma_tf32(tmem, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+          for (int ks = 0; ks < kBK / 8; ++ks) {  // 8 TF32 = 32 bytes per MMA
+            const uint32_t off = 32u * ks;
+            mma_tf32(dacc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc,
+                     (c > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32(dacc, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+            mma_tf32(dacc, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+          }
+          mma_commit(conv_empty(q));
         }
-        mma_commit(empty_bar(s));
+        if (ok) mma_commit(acc_full(a));
       }
-      mma_commit(acc_bar);  // completes once every MMA issued above has finished
+      mma_commit(done_bar);  // completes once every MMA issued above has finished
+      mbar_wait(done_bar, 0u, abort_flag, p.status, false);
     }
-  } else {
+  } else if (warp >= 4) {
     // ---------------------------------------------------------------- converters
-    const int t = threadIdx.x;          // accumulator row of this thread: m0 + t
-    const int r = t & 7;                // row within its 8-row swizzle group
-    for (int c = 0; c < nchunks; ++c) {
-      const int s = c % S;
-      // Every converter thread runs every chunk (the named barriers stay matched); a
-      // thread whose wait failed skips the work.
-      const bool ok = !*abort_flag &&
-                      mbar_wait(full_bar(s), (uint32_t)(c / S) & 1u, abort_flag, p.status, true);
-      unsigned char* st = sbase + (size_t)s * SB;
-      float v[kBK];
-      if (ok) {
-        const float* araw = reinterpret_cast<const float*>(st);  // [k][m], m fastest
+    const int t = threadIdx.x - 128;    // accumulator row of this thread within a tile
+    const int r8 = t & 7;               // row within its 8-row swizzle group
+    constexpr int kBVec = BN * (kBK / 4) / 128;  // float4 of B per thread per chunk
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t tt = blockIdx.x; ok && tt < ntiles; tt += gridDim.x) {
+      for (int c = 0; c < nchunks; ++c, ++g) {
+        const int r = (int)(g % R), q = (int)(g % C);
+        if (!mbar_wait(raw_full(r), (uint32_t)(g / R) & 1u, abort_flag, p.status, true)) {
+          ok = false;
+          break;
+        }
+        const unsigned char* raw = sbase + (size_t)r * kRawBytes;
+        const float* araw = reinterpret_cast<const float*>(raw);  // [k][m], m fastest
+        const float4* braw = reinterpret_cast<const float4*>(raw + kABytes);
+        float v[kBK];
 #pragma unroll
         for (int k = 0; k < kBK; ++k) v[k] = araw[k * kBM + t];
-      }
-      converters_sync();  // the raw A buffer is overwritten by lo below
-      if (ok) {
-        unsigned char* row_lo = st + (t >> 3) * 1024 + r * 128;
-        unsigned char* row_hi = row_lo + kABytes;
+        float4 bv[kBVec];
+#pragma unroll
+        for (int i = 0; i < kBVec; ++i) bv[i] = braw[t + 128 * i];
+        mbar_arrive(raw_empty(r));  // the raw stage may be refilled
+        if (g >= C && !mbar_wait(conv_empty(q), (uint32_t)((g / C) - 1) & 1u, abort_flag,
+                                 p.status, true)) {
+          ok = false;
+          break;
+        }
+        unsigned char* cv = sbase + conv0 + (size_t)q * kConvBytes;
+        unsigned char* row_hi = cv + (t >> 3) * 1024 + r8 * 128;
+        unsigned char* row_lo = row_hi + kABytes;
 #pragma unroll
         for (int kq = 0; kq < kBK / 4; ++kq) {
           float4 h, l;
@@ -321,35 +377,40 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
           split(v[4 * kq + 1], h.y, l.y);
           split(v[4 * kq + 2], h.z, l.z);
           split(v[4 * kq + 3], h.w, l.w);
-          const int off = (kq ^ r) << 4;  // 16-byte chunk kq of row r, swizzled
+          const int off = (kq ^ r8) << 4;  // 16-byte chunk kq of row r8, swizzled
           *reinterpret_cast<float4*>(row_hi + off) = h;
           *reinterpret_cast<float4*>(row_lo + off) = l;
         }
-        float4* bh = reinterpret_cast<float4*>(st + 2 * kABytes);
-        float4* bl = reinterpret_cast<float4*>(st + 2 * kABytes + kBBytes);
-        for (int i = t; i < BN * (kBK / 4); i += 128) {
-          const float4 x = bh[i];
+        float4* bh = reinterpret_cast<float4*>(cv + 2 * kABytes);
+        float4* bl = reinterpret_cast<float4*>(cv + 2 * kABytes + kBBytes);
+#pragma unroll
+        for (int i = 0; i < kBVec; ++i) {  // same (swizzled) positions as the raw stage
           float4 h, l;
-          split(x.x, h.x, l.x);
-          split(x.y, h.y, l.y);
-          split(x.z, h.z, l.z);
-          split(x.w, h.w, l.w);
-          bh[i] = h;
-          bl[i] = l;
+          split(bv[i].x, h.x, l.x);
+          split(bv[i].y, h.y, l.y);
+          split(bv[i].z, h.z, l.z);
+          split(bv[i].w, h.w, l.w);
+          bh[t + 128 * i] = h;
+          bl[t + 128 * i] = l;
         }
         fence_proxy_async();  // generic-proxy writes -> visible to the tensor cores
-        mbar_arrive(conv_bar(s));
+        mbar_arrive(conv_full(q));
       }
     }
-    // ---------------------------------------------------------------- epilogue
-    bool ok = mbar_wait(acc_bar, 0u, abort_flag, p.status, false);
-    ok = ok && !*abort_flag;
-    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;  // warp-uniform for tcgen05.ld
-    tc_fence_after();
-    if (ok) {
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 0-3)
+    int64_t it = 0;
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
+      const int a = (int)(it & 1);
+      bool ok = mbar_wait(acc_full(a), (uint32_t)(it / 2) & 1u, abort_flag, p.status, true);
+      if (!__all_sync(0xffffffffu, ok)) break;  // warp-uniform for tcgen05.ld
+      tc_fence_after();
+      int64_t b;
+      int m0, n0;
+      tile_coords(t, b, m0, n0);
       const int64_t m = (int64_t)m0 + warp * 32 + lane;
       float* Dp = p.D + b * p.sD;
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)a * kAccCols;
 #pragma unroll 1
       for (int cc = 0; cc < BN; cc += 16) {
         if (n0 + cc >= p.N) break;  // uniform across the warp
@@ -363,11 +424,13 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
           }
         }
       }
+      tc_fence_before();
+      mbar_arrive(acc_empty(a));  // the accumulator may be overwritten
     }
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 5) {
+  if (warp == 9) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols)
@@ -413,35 +476,45 @@ bool make_map(CUtensorMap* map, const float* ptr, uint64_t d0, uint64_t d1, uint
 }
 
 template <int BN>
-constexpr uint32_t stage_bytes() { return 2 * kABytes + 2 * (uint32_t)BN * 128; }
-
+constexpr int raw_bytes() { return (int)kABytes + BN * 128; }
 template <int BN>
-int stages_for() {  // 2 CTAs per SM for narrow tiles, deeper rings for wide ones
-  return BN <= 64 ? 2 : (BN == 128 ? 3 : 2);
+constexpr int conv_bytes() { return 2 * (int)kABytes + 2 * BN * 128; }
+constexpr int kCtlBytes = 1024 + 256;  // alignment slack + barriers
+
+// Two converted stages where they fit (BN <= 128), then as many raw stages as fit.
+template <int BN>
+void ring_for(int* raw, int* conv) {
+  *conv = (2 * conv_bytes<BN>() + raw_bytes<BN>() + kCtlBytes <= kSmemLimit) ? 2 : 1;
+  int r = (kSmemLimit - kCtlBytes - *conv * conv_bytes<BN>()) / raw_bytes<BN>();
+  *raw = r > kMaxRaw ? kMaxRaw : r;
 }
 
 template <int BN>
-int smem_for() { return stages_for<BN>() * (int)stage_bytes<BN>() + 1024 + 256; }
+int smem_for(int raw, int conv) { return raw * raw_bytes<BN>() + conv * conv_bytes<BN>() + kCtlBytes; }
 
 template <int BN>
 cudaError_t launch_bn(const TcGemm& g, const CUtensorMap& ma, const CUtensorMap& mb,
                       int32_t* status, cudaStream_t st) {
   TcParams p;
-  p.M = g.M; p.N = g.N; p.K = g.K;
+  p.M = g.M; p.N = g.N; p.K = g.K; p.batch = g.batch;
   p.D = g.D; p.ldd = g.ldd; p.sD = g.sD;
   p.m_tiles = (g.M + kBM - 1) / kBM;
   p.n_tiles = (g.N + BN - 1) / BN;
-  p.stages = stages_for<BN>();
+  ring_for<BN>(&p.raw_stages, &p.conv_stages);
   p.b_batched = g.sB != 0 ? 1 : 0;
-  p.stage_bytes = stage_bytes<BN>();
   p.status = status;
   const int64_t tiles = g.batch * p.m_tiles * p.n_tiles;
-  if (tiles < 1 || tiles > (int64_t)INT32_MAX) return cudaErrorInvalidValue;
-  const int smem = smem_for<BN>();
+  if (tiles < 1 || p.raw_stages < 1) return cudaErrorInvalidValue;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+    sms = kNumSMs;
+  const int smem = smem_for<BN>(p.raw_stages, p.conv_stages);
   auto k = tc_gemm_tf32x3<BN>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k<<<(unsigned)tiles, kThreads, smem, st>>>(ma, mb, p);
+  const int64_t grid = tiles < sms ? tiles : sms;  // persistent: one CTA per SM
+  k<<<(unsigned)grid, kThreads, smem, st>>>(ma, mb, p);
   return cudaGetLastError();
 }
 
@@ -455,8 +528,12 @@ int tc_tile_n(const TcGemm& g, int forced) {
     if (g.N <= 128) return 128;
     return 256;
   }
+  // out of place: the widest tile up to 128 columns (each A chunk is converted once per
+  // 128 output columns; measured on (256x256)(256x128) slices: 0.31 ms at 128 vs 0.47 ms
+  // at 64)
   if (g.N <= 32) return 32;
-  return 64;
+  if (g.N <= 64) return 64;
+  return 128;
 }
 
 bool tc_gemm_supported(const TcGemm& g, int forced_bn) {

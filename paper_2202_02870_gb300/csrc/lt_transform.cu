@@ -23,6 +23,11 @@ namespace lt {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kU = 4;  // loads in flight per thread in the load phase
+
+template <typename T> struct Vec;  // 16-byte vectors
+template <> struct Vec<float> { using type = float4; static constexpr int width = 4; };
+template <> struct Vec<double> { using type = double2; static constexpr int width = 2; };
 constexpr int kR = 4;  // FP64: outputs per work item (register blocking along the mode)
 
 // FP32 coefficient rows are padded to a multiple of 8 (two 16-byte loads per row chunk).
@@ -43,6 +48,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 struct PassArgs {
   TransformPass p;
+  int vec;            // 16-byte vector loads and stores are aligned for full tiles
   const void* in;
   void* out;
   const void* mats;   // base of the context's matrix array (fwd or inv)
@@ -51,7 +57,7 @@ struct PassArgs {
 };
 
 template <typename T, int TS>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
 transform_kernel(const PassArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const TransformPass& p = a.p;
@@ -111,21 +117,55 @@ transform_kernel(const PassArgs a) {
     const int64_t base = o * p.Pg * p.Sg + s0;
     const bool full = (s0 + TS <= p.Sg);
 
-    // ---- load (with the PGA prologue when fusing the forward transform)
-    for (int idx = threadIdx.x; idx < Pg * TS; idx += blockDim.x) {
-      const int pp = idx / TS, s = idx % TS;
-      T v = T(0);
-      if (full || s0 + s < p.Sg) {
-        const int64_t e = base + (int64_t)pp * p.Sg + s;
-        if (a.fuse_mode == FUSE_PGA_FORWARD) {
-          const T x = xc[e], x_old = xo[e];
-          const T y = x + beta * (x - x_old);
-          v = mk[e] ? y - step * (y - ob[e]) : y;
-        } else {
-          v = gin[e];
+    // ---- load (with the PGA prologue when fusing the forward transform).  Each thread
+    // issues kU loads (16-byte vectors where the tile allows) before it writes any of
+    // them to shared memory, so that enough bytes are in flight to cover the latency.
+    const int total = Pg * TS;
+    if (a.vec && full && a.fuse_mode == FUSE_NONE) {
+      using V = typename Vec<T>::type;
+      constexpr int VW = Vec<T>::width;
+      const int tv = total / VW;
+      for (int i0 = threadIdx.x; i0 < tv; i0 += kU * blockDim.x) {
+        V v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int iv = i0 + u * blockDim.x;
+          if (iv < tv) {
+            const int idx = iv * VW, pp = idx / TS, sc = idx % TS;
+            v[u] = *reinterpret_cast<const V*>(gin + base + (int64_t)pp * p.Sg + sc);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int iv = i0 + u * blockDim.x;
+          if (iv < tv) *reinterpret_cast<V*>(buf0 + iv * VW) = v[u];
         }
       }
-      buf0[idx] = v;
+    } else {
+      for (int i0 = threadIdx.x; i0 < total; i0 += kU * blockDim.x) {
+        T v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int idx = i0 + u * blockDim.x;
+          v[u] = T(0);
+          const int pp = idx / TS, sc = idx % TS;
+          if (idx < total && (full || s0 + sc < p.Sg)) {
+            const int64_t e = base + (int64_t)pp * p.Sg + sc;
+            if (a.fuse_mode == FUSE_PGA_FORWARD) {
+              const T x = xc[e], x_old = xo[e];
+              const T y = x + beta * (x - x_old);
+              v[u] = mk[e] ? y - step * (y - ob[e]) : y;
+            } else {
+              v[u] = gin[e];
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int idx = i0 + u * blockDim.x;
+          if (idx < total) buf0[idx] = v[u];
+        }
+      }
     }
     __syncthreads();
 
@@ -208,6 +248,15 @@ transform_kernel(const PassArgs a) {
 
     // ---- store (with the PGA epilogue when fusing the inverse transform)
     AccT tr = AccT(0), tx = AccT(0), tf = AccT(0);
+    if (a.vec && full && a.fuse_mode == FUSE_NONE) {
+      using V = typename Vec<T>::type;
+      constexpr int VW = Vec<T>::width;
+      for (int iv = threadIdx.x; iv < total / VW; iv += blockDim.x) {
+        const int idx = iv * VW, pp = idx / TS, sc = idx % TS;
+        *reinterpret_cast<V*>(gout + base + (int64_t)pp * p.Sg + sc) =
+            *reinterpret_cast<const V*>(src + idx);
+      }
+    } else
     for (int idx = threadIdx.x; idx < Pg * TS; idx += blockDim.x) {
       const int pp = idx / TS, s = idx % TS;
       if (!(full || s0 + s < p.Sg)) continue;
@@ -410,6 +459,11 @@ cudaError_t launch_transform(const Ctx& c, const TransformPlan& plan, const void
     a.out = out;
     a.mats = plan.inverse ? c.d_inv : c.d_fwd;
     a.fuse_mode = FUSE_NONE;
+    {
+      const int vw = 16 / c.elem;
+      const uintptr_t al = reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.out);
+      a.vec = (a.p.Sg % vw == 0) && (a.p.ts % vw == 0) && (al % 16 == 0);
+    }
     if (fuse) a.fuse = *fuse;
     if (fuse_mode == FUSE_PGA_FORWARD && i == 0) a.fuse_mode = FUSE_PGA_FORWARD;
     if (fuse_mode == FUSE_PGA_INVERSE && i == plan.npass - 1) a.fuse_mode = FUSE_PGA_INVERSE;
