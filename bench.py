@@ -11,9 +11,14 @@ value     PGA iterations per second of the plain FP64 path, summed over ranks, i
           resident in HBM.  L2 is flushed (a 512 MiB write) between timed steps.
 e2e       the same metric through the C ABI with host buffers: the pinned-host mask and
           observations are copied in and the result copied out inside every step.
-mixed     the LT_MIXED path on the same inputs (FP32 data; the mode-32 products on the
-          tcgen05 tensor cores in split TF32 x 3), with its relative error against
-          the FP64 result of the same run; fp32: the same for the all-SIMT FP32 path.
+mixed     the LT_MIXED path on the same inputs (FP32 data; modes below 64 stay in the
+          fused SIMT transform passes, so here it runs the FP32 kernels), with its
+          relative error against the FP64 result of the same run; fp32: the same for
+          the LT_FP32 context.
+batched   the 64 uneven completion problems in LT_MIXED (those with I4 = 64 put their
+          mode-4 products on the tcgen05 tensor cores) as one graph-captured call.
+product_256x256x16x16x8  the fifth-order *_L-product (LT_MIXED and FP32): the face-wise
+          GEMM on the tcgen05 tensor cores (split TF32 x 3) against the HBM roofline.
 roofline  the Jacobi SVT kernel (dominant): executed-flop count reported by the kernel
           / its CUDA-event time over the timed steps, against the FP64 FMA peak measured
           on this GPU (ALU-bound: the FP64 pipe).
@@ -291,6 +296,11 @@ def run_ours(args):
     if args.batched_steps > 0:
         batched = run_batched_leg(args, dev, ws)
 
+    # ---------------- the fifth-order *_L-product (face-wise GEMM on the tensor cores)
+    product = None
+    if args.product_steps > 0 and rank == 0:
+        product = product5_leg(["mixed", "fp32"], args.product_steps, 2)
+
     # ---------------- e2e: host buffers through the C ABI, copies inside each step
     mask_h = torch.from_numpy(np.ascontiguousarray(c["mask"].ravel(order="F"))).reshape(tshape).pin_memory()
     obs_h = obs64.cpu().pin_memory()
@@ -359,6 +369,7 @@ def run_ours(args):
             "mixed": mixed_leg,
             "fp32": fp32_leg,
             "batched": batched,
+            "product_256x256x16x16x8": product,
             "roofline": {"kernel": "jacobi_svt (FP64)", "bound": "alu",
                          "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
                          "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
@@ -452,6 +463,7 @@ def run_case(args):
         tuple(reversed(a.shape))).to(dev)
     ctx = lt.Context([3, 32], [lt.lt_make_dct(3), lt.lt_make_dct(32)], prec)
     lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_GROUP, args.jacobi_group)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_BLOCK, args.jacobi_pairwise)
     if args.case == "svt":
         G = to_dev(c["mask"] * np.random.default_rng(1).standard_normal(c["mask"].shape))
         D = torch.empty_like(G)
@@ -476,68 +488,85 @@ def run_case(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     print(json.dumps({"case": args.case, "precision": args.precision,
-                      "jacobi_group": args.jacobi_group, "ms_per_call": ms,
+                      "jacobi_group": args.jacobi_group, "jacobi_pairwise": args.jacobi_pairwise,
+                      "ms_per_call": ms,
                       f"{unit}_per_s": units / (ms / 1e3)}))
 
 
-def run_product5(args):
-    """--case product5: the fifth-order *_L-product 256x256x16x16x8 times
-    256x128x16x16x8 (U[-1,1]; L_k = Q_k diag(d_k), cond 1e2 each) through lt_product:
-    three transforms (modes 16, 16, 8) and the face-wise GEMM of 2048 slices of
-    (256x256)(256x128).  Reports per-call time, the per-family event times and the
-    GEMM kernel against the HBM roofline (algorithmic bytes: read A_hat and B_hat once,
-    write C_hat once) and, for LT_MIXED, the tensor-pipe rate of the three TF32
-    products it issues."""
+def product5_leg(precisions, steps, warmup, tile_n=0):
+    """The fifth-order *_L-product 256x256x16x16x8 times 256x128x16x16x8 (U[-1,1];
+    L_k = Q_k diag(d_k), cond 1e2 each) through lt_product: three transforms (modes
+    16, 16, 8) and the face-wise GEMM of 2048 slices of (256x256)(256x128).  Per
+    precision: per-call time, per-family event times, and the GEMM kernel against the
+    HBM roofline (algorithmic bytes: read L(A) and L(B) once, write L(C) once) with, for
+    LT_MIXED, the tensor-pipe rate of the three TF32 products it issues."""
     import torch
     from paper_2202_02870_gb300 import lt, synth
-    prec = {"fp64": lt.LT_FP64, "fp32": lt.LT_FP32, "mixed": lt.LT_MIXED}[args.precision]
-    dt = torch.float64 if prec == lt.LT_FP64 else torch.float32
     c = synth.config3()
     dev = torch.device("cuda", 0)
-    to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.ravel(order="F"))).to(dt).reshape(
-        tuple(reversed(a.shape))).to(dev)
-    A, B = to_dev(c["A"]), to_dev(c["B"])
-    del c["A"], c["B"]
-    ctx = lt.Context([16, 16, 8], [np.asarray(m) for _, m in c["transforms"]], prec)
-    if args.tc_tile_n:
-        lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_TILE_N, args.tc_tile_n)
-    Cd = torch.empty((8, 16, 16, 128, 256), dtype=dt, device=dev)
-    ws = torch.empty(lt.lt_workspace_size(ctx, lt.LT_OP_PRODUCT, 256, 256, 128), dtype=torch.uint8,
-                     device=dev)
-    run = lambda: lt.lt_product(ctx, A, B, Cd, ws=ws)
-    for _ in range(args.warmup):
-        run()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        run()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    lt.lt_ctx_get_stats(ctx, reset=True)
-    lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 1)
-    for _ in range(args.steps):
-        run()
-    st = lt.lt_ctx_get_stats(ctx, reset=True)
     peaks = load_peaks()
-    g = st["gemm"]
-    g_ms = g["ms"] / max(g["launches"], 1)
-    gemm_bytes = g["bytes"] / max(g["launches"], 1)
-    gemm_flops = g["flops"] / max(g["launches"], 1)
-    line = {"case": "product5", "precision": args.precision, "ms_per_call": round(ms, 4),
-            "products_per_s": round(1e3 / ms, 3),
-            "kernels_ms_per_call": {k: round(st[k]["ms"] / args.steps, 4)
-                                    for k in ("transform", "gemm", "aux")},
-            "tc_launches_per_call": st["tc_launches"] / args.steps,
-            "gemm_roofline": {"bound": "hbm", "achieved": round(gemm_bytes / g_ms / 1e6, 1),
-                              "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                              "frac": round(gemm_bytes / g_ms / 1e6 / peaks.get("hbm_gbs", 6800.0), 4),
-                              "algorithmic_bytes": gemm_bytes, "ms_per_launch": round(g_ms, 4),
-                              "tflops_algorithmic": round(gemm_flops / g_ms / 1e9, 2)}}
-    if prec == lt.LT_MIXED:
-        line["gemm_roofline"]["tflops_issued_tf32x3"] = round(3 * gemm_flops / g_ms / 1e9, 2)
-    print(json.dumps(line))
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    host = {"A": c["A"], "B": c["B"]}
+    out = {}
+    for name in precisions:
+        prec = {"fp64": lt.LT_FP64, "fp32": lt.LT_FP32, "mixed": lt.LT_MIXED}[name]
+        dt = torch.float64 if prec == lt.LT_FP64 else torch.float32
+        to_dev = lambda a: torch.from_numpy(np.ascontiguousarray(a.ravel(order="F"))).to(dt).reshape(
+            tuple(reversed(a.shape))).to(dev)
+        A, B = to_dev(host["A"]), to_dev(host["B"])
+        ctx = lt.Context([16, 16, 8], [np.asarray(m) for _, m in c["transforms"]], prec)
+        if tile_n:
+            lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_TILE_N, tile_n)
+        Cd = torch.empty((8, 16, 16, 128, 256), dtype=dt, device=dev)
+        ws = torch.empty(lt.lt_workspace_size(ctx, lt.LT_OP_PRODUCT, 256, 256, 128),
+                         dtype=torch.uint8, device=dev)
+        run = lambda: lt.lt_product(ctx, A, B, Cd, ws=ws)
+        for _ in range(warmup):
+            run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        lt.lt_ctx_get_stats(ctx, reset=True)
+        lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 1)
+        for _ in range(steps):
+            run()
+        st = lt.lt_ctx_get_stats(ctx, reset=True)
+        g = st["gemm"]
+        g_ms = g["ms"] / max(g["launches"], 1)
+        gemm_bytes = g["bytes"] / max(g["launches"], 1)
+        gemm_flops = g["flops"] / max(g["launches"], 1)
+        tr = st["transform"]
+        leg = {"ms_per_call": round(ms, 4), "products_per_s": round(1e3 / ms, 3),
+               "kernels_ms_per_call": {k: round(st[k]["ms"] / steps, 4)
+                                       for k in ("transform", "gemm", "aux")},
+               "tc_launches_per_call": st["tc_launches"] / steps,
+               "gemm_roofline": {"bound": "hbm", "achieved": round(gemm_bytes / g_ms / 1e6, 1),
+                                 "peak": hbm, "unit": "GB/s",
+                                 "frac": round(gemm_bytes / g_ms / 1e6 / hbm, 4),
+                                 "algorithmic_bytes": gemm_bytes, "ms_per_launch": round(g_ms, 4),
+                                 "tflops_algorithmic": round(gemm_flops / g_ms / 1e9, 2)},
+               "transform_roofline": {"bound": "hbm",
+                                      "achieved": round(tr["bytes"] / max(tr["ms"], 1e-9) / 1e6, 1),
+                                      "peak": hbm, "unit": "GB/s",
+                                      "frac": round(tr["bytes"] / max(tr["ms"], 1e-9) / 1e6 / hbm, 4),
+                                      "tflops_algorithmic": round(tr["flops"] / max(tr["ms"], 1e-9) / 1e9, 2)}}
+        if prec == lt.LT_MIXED:
+            leg["gemm_roofline"]["tflops_issued_tf32x3"] = round(3 * gemm_flops / g_ms / 1e9, 2)
+        out[name] = leg
+        del A, B, Cd, ws, ctx
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_product5(args):
+    """--case product5: the fifth-order product leg alone, one precision."""
+    leg = product5_leg([args.precision], args.steps, args.warmup, args.tc_tile_n)[args.precision]
+    print(json.dumps({"case": "product5", "precision": args.precision, **leg}))
 
 
 def run_transform5(args):
@@ -629,6 +658,8 @@ def main():
                     help="timed calls of the 64-problem batch (0 skips the batched leg)")
     ap.add_argument("--batched-iters", type=int, default=4,
                     help="PGA iterations per call of the 64-problem batch")
+    ap.add_argument("--product-steps", type=int, default=5,
+                    help="timed calls of the fifth-order product leg (0 skips it)")
     ap.add_argument("--case", default="pga",
                     choices=["pga", "svt", "product", "product5", "transform5"],
                     help="pga: the benchmark line; svt/product: single-operation runs "
@@ -636,6 +667,9 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--tc-tile-n", type=int, default=0, choices=[0, 32, 64, 128, 256],
                     help="LT_MIXED tensor-core tile width (0: the library's choice)")
+    ap.add_argument("--jacobi-pairwise", type=int, default=0, choices=[0, 1, 2],
+                    help="1: rotate column pairs straight through shared memory (no "
+                         "register blocks)")
     ap.add_argument("--jacobi-group", type=int, default=0, choices=[0, 8, 16, 32],
                     help="lanes per Jacobi column pair (0: the planner's choice)")
     args = ap.parse_args()

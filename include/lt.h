@@ -98,7 +98,10 @@ typedef enum {
                                 default) lets the planner choose from min(I1, I2) */
   LT_OPT_JACOBI_BLOCK = 5,   /* SVT kernel: 1 = rotate column pairs straight through
                                 shared memory; 0 (default) = FP32 contexts hold blocks of
-                                2-4 columns per group in registers where they fit */
+                                2-4 columns per group in registers where they fit; 2 =
+                                FP32 register blocks with the group width forced by
+                                LT_OPT_JACOBI_GROUP (8: blocks of 2, n <= 144; 16: blocks
+                                of 4 (n <= 144) or 2; 32: blocks of 2) */
   LT_OPT_TC_MODE_MIN = 6,    /* LT_MIXED: a mode k >= 4 with I_k >= this value (default
                                 64; modes above 224 never) is applied in a pass of its own
                                 on the tensor cores; mode 3 and smaller modes are applied

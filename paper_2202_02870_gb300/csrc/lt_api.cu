@@ -393,7 +393,7 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
       c->profile = value != 0.0;
       return LT_OK;
     case LT_OPT_JACOBI_BLOCK:
-      if (!(value == 0 || value == 1)) return LT_ERR_ARG;
+      if (!(value == 0 || value == 1 || value == 2)) return LT_ERR_ARG;
       c->jacobi_pairwise = (int)value;
       return LT_OK;
     case LT_OPT_JACOBI_GROUP:

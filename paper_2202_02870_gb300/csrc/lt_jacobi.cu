@@ -429,6 +429,7 @@ struct SvtShape { int G, B; const int* E; int nE; };
 const int kBlk16x4[] = {1, 2, 3, 4, 5, 6, 7, 8, 9};
 const int kBlk16x2[] = {12, 18};
 const int kBlk32x2[] = {12, 18};
+const int kBlk8x2[] = {6, 12, 18};
 const int kF8[] = {2, 4, 6, 8, 12, 18, 24};
 const int kF16[] = {16, 24};
 const int kF32[] = {20, 24, 28, 32};
@@ -445,6 +446,13 @@ int pick_E(const int* set, int cnt, int need) {
 // Choose (G, B, E) for n columns.  force_g != 0 fixes G (pairwise); pairwise != 0
 // disables register blocking.  Returns false when no instantiation holds n.
 bool svt_shape(int n, int elem, int force_g, int pairwise, int* G, int* B, int* E) {
+  if (elem == 4 && pairwise == 2) {  // register blocks with the forced group width
+    if (force_g == 8) { *G = 8; *B = 2; *E = pick_E(kBlk8x2, 3, (n + 7) / 8); return *E > 0; }
+    if (force_g == 16 && n <= 144) { *G = 16; *B = 4; *E = pick_E(kBlk16x4, 9, (n + 15) / 16); return *E > 0; }
+    if (force_g == 16) { *G = 16; *B = 2; *E = pick_E(kBlk16x2, 2, (n + 15) / 16); return *E > 0; }
+    if (force_g == 32) { *G = 32; *B = 2; *E = pick_E(kBlk32x2, 2, (n + 31) / 32); return *E > 0; }
+    return false;
+  }
   if (elem == 4 && !force_g && !pairwise && n <= 576) {
     if (n <= 144) { *G = 16; *B = 4; *E = pick_E(kBlk16x4, 9, (n + 15) / 16); }
     else if (n <= 288) { *G = 16; *B = 2; *E = pick_E(kBlk16x2, 2, (n + 15) / 16); }
@@ -571,11 +579,11 @@ cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io
     // it does not hold
     using L = cudaError_t (*)(const JArgs&, int, cudaStream_t);
     static const L f32[] = {jac::launch_svt_f32_blk_a, jac::launch_svt_f32_blk_b,
-                            jac::launch_svt_f32_blk_c, jac::launch_svt_f32_pw_a,
-                            jac::launch_svt_f32_pw_b};
+                            jac::launch_svt_f32_blk_c, jac::launch_svt_f32_blk_d,
+                            jac::launch_svt_f32_pw_a, jac::launch_svt_f32_pw_b};
     static const L f64[] = {jac::launch_svt_f64_a, jac::launch_svt_f64_b, jac::launch_svt_f64_c};
     const L* tab = c.elem == 8 ? f64 : f32;
-    const int cnt = c.elem == 8 ? 3 : 5;
+    const int cnt = c.elem == 8 ? 3 : 6;
     for (int i = 0; i < cnt; ++i) {
       const cudaError_t e = tab[i](a, grid, st);
       if (e != cudaErrorNotSupported) return e;

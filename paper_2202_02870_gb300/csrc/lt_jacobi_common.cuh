@@ -108,6 +108,7 @@ constexpr int kMaxThreadsBlocked = 512;  // register-blocked FP32 sweeps: 128 re
 cudaError_t launch_svt_f32_blk_a(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_blk_b(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_blk_c(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f32_blk_d(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_pw_a(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_pw_b(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f64_a(const JArgs& a, int grid, cudaStream_t st);

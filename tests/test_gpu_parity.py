@@ -231,6 +231,26 @@ def test_svt_kernel_variants(prec, group, pairwise, shape):
     assert lt.lt_last_device_status(ctx) == 0
 
 
+@pytest.mark.parametrize("group", [8, 16, 32])
+@pytest.mark.parametrize("shape", [(37, 23), (144, 176)])
+def test_svt_forced_register_blocks(group, shape):
+    """FP32 register-blocked sweeps with a forced group width (LT_OPT_JACOBI_BLOCK = 2:
+    8-lane groups with blocks of 2 columns, 16 with blocks of 4, 32 with blocks of 2)
+    against the oracle."""
+    rng = np.random.default_rng(shape[0] + group)
+    transforms = [("dct", 2)]
+    full = tuple(shape) + (2,)
+    A = rng.standard_normal(full)
+    ctx = make_ctx(transforms, lt.LT_FP32)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_GROUP, group)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_BLOCK, 2)
+    D = empty_dev(full, torch.float32)
+    lt.lt_svt(ctx, to_dev(A, torch.float32), 1.0, D)
+    torch.cuda.synchronize()
+    assert rel(from_dev(D, full), O.svt(A, 1.0, oracle_mats(transforms))) <= TOL[lt.LT_FP32]
+    assert lt.lt_last_device_status(ctx) == 0
+
+
 @pytest.mark.parametrize("prec,scale", [(lt.LT_FP64, 1e-150), (lt.LT_FP64, 1e-30),
                                         (lt.LT_FP64, 1e30), (lt.LT_FP64, 1e150),
                                         (lt.LT_FP32, 1e-25), (lt.LT_FP32, 1e25)])
