@@ -526,11 +526,14 @@ lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan
       const int want = (jp.npad / 2 + ppw - 1) / ppw;
       jp.threads = 32 * std::max(4, std::min(maxw, want));
     }
+    // the kernel's static shared memory (per-pair scalars of the FP64 sweeps, counters)
+    // takes up to ~4 KB beside the dynamic part
+    const size_t cap = (size_t)kSmemOptin - 5120;
     need = c.elem == 8 ? svt_smem<double>(jp) : svt_smem<float>(jp);
-    if (need > (size_t)kSmemOptin - 1024) {
+    if (need > cap) {
       jp.w_in_smem = false;
       need = c.elem == 8 ? svt_smem<double>(jp) : svt_smem<float>(jp);
-      if (need > (size_t)kSmemOptin - 1024) return LT_ERR_SHAPE;
+      if (need > cap) return LT_ERR_SHAPE;
     }
   } else {
     jp.ld = jp.m | 1;  // odd leading dimension: conflict-free transposed stores

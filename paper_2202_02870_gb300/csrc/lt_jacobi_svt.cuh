@@ -180,6 +180,12 @@ jacobi_svt_kernel(const JArgs a) {
     isc = reinterpret_cast<T*>(sp); sp += sizeof(T) * np;
   }
   __shared__ int s_piv, s_count, s_rot;
+  // FP64 scaled sweeps: per-pair scalars of one batch of pairs (dot product; update
+  // coefficients; rescale factors; rotate or not), so that the rotation parameters are
+  // computed once per pair by one thread instead of on every lane of the pair's group
+  constexpr int kPairs = kScaled ? MAXT / G : 1;
+  __shared__ T s_pg[kPairs], s_pa[kPairs], s_pb[kPairs], s_sx[kPairs], s_sy[kPairs];
+  __shared__ int s_pr[kPairs];
   __shared__ unsigned long long s_maxbits;
   __shared__ T s_alpha, s_beta, s_v0;
 
@@ -506,54 +512,84 @@ jacobi_svt_kernel(const JArgs a) {
             g = fma(x[e], y[e], g);
           }
           g = group_sum<G>(g);
-          const T al = active ? nrm2[i] : T(0), be = active ? nrm2[j] : T(0);
           if constexpr (kScaled) {
             // columns d_i x~, d_j y~: the rotation x' = c (x - t y), y' = c (y + t x)
             // becomes x~' = x~ - t (d_j / d_i) y~, y~' = y~ + t (d_i / d_j) x~ with
             // d_i' = c d_i, d_j' = c d_j: two FP64 multiply-adds per row instead of four
             // (Rutishauser-style scaled rotations; the scales are multiplied out at each
-            // sweep start and whenever one falls below 2^-64)
-            const T di = dsc[i], dj = dsc[j];
-            g *= di * dj;
-            if (al > T(0) && be > T(0) && g * g > tol2 * al * be) {
-              T cs, ic, t;
-              rotation_scaled(al, be, g, cs, ic, t);
-              const T ei = isc[i], ej = isc[j];
-              const T alpha = t * dj * ei, beta = t * di * ej;
-              T di2 = di * cs, dj2 = dj * cs, ei2 = ei * ic, ej2 = ej * ic;
+            // sweep start and whenever one falls below 2^-64).  Three phases: the groups'
+            // dot products, the per-pair parameters (one thread per pair), the groups'
+            // column updates.
+            if (gl == 0) s_pg[grp] = g;
+            __syncthreads();
+            const int batch = min(ngrp, npairs - k0);
+            for (int q = threadIdx.x; q < batch; q += blockDim.x) {
+              const int kq = k0 + q;
+              int pi, pj;
+              if (kq == 0) {
+                pi = cfix;
+                pj = rnd;
+              } else {
+                pi = rnd + kq;
+                if (pi >= cfix) pi -= cfix;
+                pj = rnd - kq;
+                if (pj < 0) pj += cfix;
+              }
+              const T al = nrm2[pi], be = nrm2[pj];
+              const T di = dsc[pi], dj = dsc[pj];
+              const T gq = s_pg[q] * (di * dj);
+              int rot = 0;
+              if (al > T(0) && be > T(0) && gq * gq > tol2 * al * be) {
+                T cs, ic, t;
+                rotation_scaled(al, be, gq, cs, ic, t);
+                const T ei = isc[pi], ej = isc[pj];
+                T di2 = di * cs, dj2 = dj * cs, ei2 = ei * ic, ej2 = ej * ic;
+                s_pa[q] = t * dj * ei;
+                s_pb[q] = t * di * ej;
+                T fx = T(1), fy = T(1);
+                if (di2 < T(0x1p-64)) { fx = di2; di2 = ei2 = T(1); }
+                if (dj2 < T(0x1p-64)) { fy = dj2; dj2 = ej2 = T(1); }
+                s_sx[q] = fx;
+                s_sy[q] = fy;
+                nrm2[pi] = al - t * gq;
+                nrm2[pj] = be + t * gq;
+                dsc[pi] = di2;
+                dsc[pj] = dj2;
+                isc[pi] = ei2;
+                isc[pj] = ej2;
+                ++nrot;
+                flag = 1;
+                rot = 1;
+              }
+              s_pr[q] = rot;
+            }
+            __syncthreads();
+            if (active && s_pr[grp]) {  // uniform over the group
+              const T alpha = s_pa[grp], beta = s_pb[grp];
 #pragma unroll
               for (int e = 0; e < E; ++e) {
                 const T xe = x[e], ye = y[e];
                 x[e] = fma(-alpha, ye, xe);
                 y[e] = fma(beta, xe, ye);
               }
-              if (di2 < T(0x1p-64)) {  // uniform over the group
+              const T fx = s_sx[grp], fy = s_sy[grp];
+              if (fx != T(1)) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) x[e] *= di2;
-                di2 = ei2 = T(1);
+                for (int e = 0; e < E; ++e) x[e] *= fx;
               }
-              if (dj2 < T(0x1p-64)) {
+              if (fy != T(1)) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) y[e] *= dj2;
-                dj2 = ej2 = T(1);
+                for (int e = 0; e < E; ++e) y[e] *= fy;
               }
 #pragma unroll
               for (int e = 0; e < E; ++e) {
                 ci[gl + G * e] = x[e];
                 cj[gl + G * e] = y[e];
               }
-              if (gl == 0) {
-                nrm2[i] = al - t * g;
-                nrm2[j] = be + t * g;
-                dsc[i] = di2;
-                dsc[j] = dj2;
-                isc[i] = ei2;
-                isc[j] = ej2;
-                ++nrot;
-              }
-              flag = 1;
             }
-          } else
+            continue;
+          }
+          const T al = active ? nrm2[i] : T(0), be = active ? nrm2[j] : T(0);
           if (al > T(0) && be > T(0) && g * g > tol2 * al * be) {
             T cs, sn, t;
             rotation_fast(al, be, g, cs, sn, t);
