@@ -18,6 +18,30 @@ __device__ __forceinline__ T warp_allsum(T v) {
   return v;
 }
 
+// Four warp-wide sums at once, every lane receiving all four: a transposed butterfly
+// (the first two levels exchange halves of the vector, so each lane adds 2 + 1 + 3 = 6
+// values instead of 4 x 5), then a broadcast from the lanes that hold each total.
+template <typename T>
+__device__ __forceinline__ void warp_allsum4(T (&w)[4]) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0;
+  T k0 = h16 ? w[2] : w[0], k1 = h16 ? w[3] : w[1];
+  const T s0 = h16 ? w[0] : w[2], s1 = h16 ? w[1] : w[3];
+  k0 += __shfl_xor_sync(full, s0, 16);
+  k1 += __shfl_xor_sync(full, s1, 16);
+  T k = h8 ? k1 : k0;
+  k += __shfl_xor_sync(full, h8 ? k0 : k1, 8);
+  k += __shfl_xor_sync(full, k, 4);
+  k += __shfl_xor_sync(full, k, 2);
+  k += __shfl_xor_sync(full, k, 1);
+  // the total of vector entry c = 2 h16 + h8 now sits on every lane with those bits
+  w[0] = __shfl_sync(full, k, 0);
+  w[1] = __shfl_sync(full, k, 8);
+  w[2] = __shfl_sync(full, k, 16);
+  w[3] = __shfl_sync(full, k, 24);
+}
+
 // (value, index) arg-max over the warp; ties go to the smaller index.  Every lane ends
 // with the result.
 template <typename T>

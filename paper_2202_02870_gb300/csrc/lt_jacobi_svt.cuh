@@ -314,10 +314,7 @@ jacobi_svt_kernel(const JArgs a) {
 #pragma unroll
           for (int u = 0; u < 4; ++u) w[u] = fma(vr, col[u][r], w[u]);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-          for (int u = 0; u < 4; ++u) w[u] += __shfl_xor_sync(0xffffffffu, w[u], o);
+        warp_allsum4(w);
 #pragma unroll
         for (int u = 0; u < 4; ++u) w[u] *= beta;
         __syncwarp();
@@ -329,21 +326,29 @@ jacobi_svt_kernel(const JArgs a) {
           for (int r = j + 1 + lane; r < m; r += 32) cu[r] = fma(-w[u], vj[r], cu[r]);
         }
         __syncwarp();
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (c0 + u >= n) continue;
-          const int c = c0 + u;
-          T* cu = col[u];
-          // downdate the remaining norm; recompute it when cancellation has eaten it
-          const T rjc = cu[j];
-          T nn = nrm2[c] - rjc * rjc;
-          if (nn <= T(0.01) * ref[c]) {
-            T sq = T(0);
-            for (int r = j + 1 + lane; r < m; r += 32) sq = fma(cu[r], cu[r], sq);
-            nn = warp_allsum(sq);
-            if (lane == 0) ref[c] = nn;
+        // downdate the remaining norms, lane u for column c0 + u; a column whose norm
+        // cancellation has eaten is recomputed by the whole warp
+        bool redo = false;
+        T nn = T(0);
+        if (lane < 4 && c0 + lane < n) {
+          const int c = c0 + lane;
+          const T rjc = W[j + (size_t)ld * c];
+          nn = nrm2[c] - rjc * rjc;
+          redo = nn <= T(0.01) * ref[c];
+          if (!redo) nrm2[c] = nn > T(0) ? nn : T(0);
+        }
+        unsigned mask = __ballot_sync(0xffffffffu, redo);
+        while (mask) {  // rare
+          const int u = __ffs(mask) - 1;
+          mask &= mask - 1;
+          const T* cu = col[u];
+          T sq = T(0);
+          for (int r = j + 1 + lane; r < m; r += 32) sq = fma(cu[r], cu[r], sq);
+          sq = warp_allsum(sq);
+          if (lane == 0) {
+            ref[c0 + u] = sq;
+            nrm2[c0 + u] = sq > T(0) ? sq : T(0);
           }
-          if (lane == 0) nrm2[c] = nn > T(0) ? nn : T(0);
         }
       }
       if (threadIdx.x == 0) W[j + (size_t)ld * j] = alpha;
@@ -707,13 +712,9 @@ jacobi_svt_kernel(const JArgs a) {
             d2 = fma(z2[lane + 32 * e], b[e], d2);
             d3 = fma(z3[lane + 32 * e], b[e], d3);
           }
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            d0 += __shfl_xor_sync(0xffffffffu, d0, o);
-            d1 += __shfl_xor_sync(0xffffffffu, d1, o);
-            d2 += __shfl_xor_sync(0xffffffffu, d2, o);
-            d3 += __shfl_xor_sync(0xffffffffu, d3, o);
-          }
+          T dv[4] = {d0, d1, d2, d3};
+          warp_allsum4(dv);
+          d0 = dv[0]; d1 = dv[1]; d2 = dv[2]; d3 = dv[3];
           if (lane == gq) yreg[s2] = d0 * nrm2[list[s2 * 32 + gq]];
           if (lane == gq + 1) yreg[s2] = d1 * nrm2[list[s2 * 32 + gq + 1]];
           if (lane == gq + 2) yreg[s2] = d2 * nrm2[list[s2 * 32 + gq + 2]];
