@@ -20,15 +20,15 @@
 //
 // Persistent kernel, one CTA per SM; a CTA takes 128 x BN output tiles of the D_b in
 // turn (column tiles fastest), K in chunks of 32 FP32 (one 128-byte row):
-//   warp 8    TMA producer (one thread): per chunk, the raw A chunk (128 x 32, M
+//   warp 12   TMA producer (one thread): per chunk, the raw A chunk (128 x 32, M
 //             fastest, no swizzle) and the B chunk (32 x BN, K fastest, 128-byte swizzle,
 //             which is the K-major canonical operand layout) into a ring of up to six
 //             raw stages, completion counted on an mbarrier (complete_tx).
-//   warps 4-7 converters (one accumulator row per thread): read a raw stage into
+//   warps 4-11 converters (an accumulator row and half of K per thread): read a raw stage into
 //             registers and release it at once, then write hi and lo of A transposed
 //             into the K-major 128-byte-swizzled layout and hi and lo of B at the raw
 //             (swizzled) positions into a ring of two converted stages.
-//   warp 9    TMEM allocation (two accumulators of BN columns) and the MMA issuer (one
+//   warp 13   TMEM allocation (two accumulators of BN columns) and the MMA issuer (one
 //             thread): per 8-deep K step three tcgen05.mma kind::tf32 (hi hi, hi lo,
 //             lo hi) into the 128 x BN FP32 accumulator of the tile; tcgen05.commit
 //             releases a converted stage and, after the last chunk, hands the
@@ -50,8 +50,9 @@ namespace {
 
 constexpr int kBM = 128;                      // tile rows (TMEM lanes)
 constexpr int kBK = 32;                       // K per chunk: one 128-byte row of FP32
-constexpr int kThreads = 320;                 // warps 0-3 epilogue, 4-7 convert, 8 loads,
-                                              // 9 allocates TMEM and issues the MMAs
+constexpr int kThreads = 448;                 // warps 0-3 epilogue, 4-11 convert, 12 loads,
+                                              // 13 allocates TMEM and issues the MMAs
+constexpr int kConv = 256;                    // converter threads
 constexpr int kMaxRaw = 6;                    // raw (TMA) stages at most
 constexpr uint32_t kABytes = kBM * kBK * 4;   // 16 KiB per A buffer
 constexpr int kSmemLimit = 232448;            // opt-in shared memory per block
@@ -232,10 +233,10 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
   if (threadIdx.x == 0) {
     for (int i = 0; i < R; ++i) {
       mbar_init(raw_full(i), 1);
-      mbar_init(raw_empty(i), 128);
+      mbar_init(raw_empty(i), kConv);
     }
     for (int i = 0; i < C; ++i) {
-      mbar_init(conv_full(i), 128);
+      mbar_init(conv_full(i), kConv);
       mbar_init(conv_empty(i), 1);
     }
     for (int i = 0; i < 2; ++i) {
@@ -246,7 +247,7 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 9) {
+  if (warp == 13) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_holder)),
                  "r"(kTmemCols)
@@ -268,7 +269,7 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
     n0 = (int)(nt * BN);
   };
 
-  if (warp == 8) {
+  if (warp == 12) {
     // ---------------------------------------------------------------- TMA producer
     if (lane == 0) {
       int last[kMaxRaw];
@@ -297,7 +298,7 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
       for (int i = 0; i < R; ++i)
         if (last[i] >= 0) mbar_wait(raw_full(i), (uint32_t)last[i] & 1u, abort_flag, p.status, false);
     }
-  } else if (warp == 9) {
+  } else if (warp == 13) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       // instruction descriptor: D FP32 (bits 4-5 = 1), A and B TF32 (bits 7-9, 10-12 =
@@ -340,9 +341,12 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
     }
   } else if (warp >= 4) {
     // ---------------------------------------------------------------- converters
-    const int t = threadIdx.x - 128;    // accumulator row of this thread within a tile
-    const int r8 = t & 7;               // row within its 8-row swizzle group
-    constexpr int kBVec = BN * (kBK / 4) / 128;  // float4 of B per thread per chunk
+    // thread t: accumulator row m = t % 128, K half h = t / 128 (16 of the 32 values)
+    const int t = threadIdx.x - 128;
+    const int mrow = t & (kBM - 1), h = t >> 7;
+    const int r8 = mrow & 7;            // row within its 8-row swizzle group
+    constexpr int kBVec = BN * (kBK / 4) / kConv;  // float4 of B per thread per chunk
+    constexpr int kHalf = kBK / 2;
     int64_t g = 0;
     bool ok = true;
     for (int64_t tt = blockIdx.x; ok && tt < ntiles; tt += gridDim.x) {
@@ -355,12 +359,12 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
         const unsigned char* raw = sbase + (size_t)r * kRawBytes;
         const float* araw = reinterpret_cast<const float*>(raw);  // [k][m], m fastest
         const float4* braw = reinterpret_cast<const float4*>(raw + kABytes);
-        float v[kBK];
+        float v[kHalf];
 #pragma unroll
-        for (int k = 0; k < kBK; ++k) v[k] = araw[k * kBM + t];
+        for (int k = 0; k < kHalf; ++k) v[k] = araw[(h * kHalf + k) * kBM + mrow];
         float4 bv[kBVec];
 #pragma unroll
-        for (int i = 0; i < kBVec; ++i) bv[i] = braw[t + 128 * i];
+        for (int i = 0; i < kBVec; ++i) bv[i] = braw[t + kConv * i];
         mbar_arrive(raw_empty(r));  // the raw stage may be refilled
         if (g >= C && !mbar_wait(conv_empty(q), (uint32_t)((g / C) - 1) & 1u, abort_flag,
                                  p.status, true)) {
@@ -368,30 +372,31 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
           break;
         }
         unsigned char* cv = sbase + conv0 + (size_t)q * kConvBytes;
-        unsigned char* row_hi = cv + (t >> 3) * 1024 + r8 * 128;
+        unsigned char* row_hi = cv + (mrow >> 3) * 1024 + r8 * 128;
         unsigned char* row_lo = row_hi + kABytes;
 #pragma unroll
-        for (int kq = 0; kq < kBK / 4; ++kq) {
-          float4 h, l;
-          split(v[4 * kq + 0], h.x, l.x);
-          split(v[4 * kq + 1], h.y, l.y);
-          split(v[4 * kq + 2], h.z, l.z);
-          split(v[4 * kq + 3], h.w, l.w);
-          const int off = (kq ^ r8) << 4;  // 16-byte chunk kq of row r8, swizzled
-          *reinterpret_cast<float4*>(row_hi + off) = h;
-          *reinterpret_cast<float4*>(row_lo + off) = l;
+        for (int qq = 0; qq < kHalf / 4; ++qq) {
+          float4 hv, lv;
+          split(v[4 * qq + 0], hv.x, lv.x);
+          split(v[4 * qq + 1], hv.y, lv.y);
+          split(v[4 * qq + 2], hv.z, lv.z);
+          split(v[4 * qq + 3], hv.w, lv.w);
+          const int kq = h * (kHalf / 4) + qq;  // 16-byte chunk of the 128-byte row
+          const int off = (kq ^ r8) << 4;       // swizzled position
+          *reinterpret_cast<float4*>(row_hi + off) = hv;
+          *reinterpret_cast<float4*>(row_lo + off) = lv;
         }
         float4* bh = reinterpret_cast<float4*>(cv + 2 * kABytes);
         float4* bl = reinterpret_cast<float4*>(cv + 2 * kABytes + kBBytes);
 #pragma unroll
         for (int i = 0; i < kBVec; ++i) {  // same (swizzled) positions as the raw stage
-          float4 h, l;
-          split(bv[i].x, h.x, l.x);
-          split(bv[i].y, h.y, l.y);
-          split(bv[i].z, h.z, l.z);
-          split(bv[i].w, h.w, l.w);
-          bh[t + 128 * i] = h;
-          bl[t + 128 * i] = l;
+          float4 hv, lv;
+          split(bv[i].x, hv.x, lv.x);
+          split(bv[i].y, hv.y, lv.y);
+          split(bv[i].z, hv.z, lv.z);
+          split(bv[i].w, hv.w, lv.w);
+          bh[t + kConv * i] = hv;
+          bl[t + kConv * i] = lv;
         }
         fence_proxy_async();  // generic-proxy writes -> visible to the tensor cores
         mbar_arrive(conv_full(q));
@@ -430,7 +435,7 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
   }
   tc_fence_before();
   __syncthreads();
-  if (warp == 9) {
+  if (warp == 13) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols)
