@@ -56,6 +56,72 @@ struct PassArgs {
   int fuse_mode;      // FUSE_* for this pass
 };
 
+// FP32 mode products of one tile: a work item is (fiber, 8 consecutive outputs
+// j0..j0+7, 4 consecutive columns); per input index i one 16-byte load of x (4 columns)
+// and two of the coefficients feed 32 FMAs.  Items are ordered output chunk first, so
+// the 8 x 4 threads of a warp mostly share j0 (uniform coefficient loads).  Returns the
+// buffer holding the result.
+template <int TS>
+__device__ __forceinline__ float* modes_f32(const TransformPass& p, const float* mats_s,
+                                            const int* moff_s, float* src, float* dst) {
+  constexpr int R = 8, C = 4;
+  const int Pg = (int)p.Pg;
+  const int cg = threadIdx.x % (TS / C);
+  const int rs = threadIdx.x / (TS / C);
+  const int nrs = blockDim.x / (TS / C);
+  for (int q = 0; q < p.nm; ++q) {
+    const int I = p.msize[q], st = p.mstride[q], Ip = padded_rows(I);
+    const float* MT = mats_s + moff_s[q];
+    const int nch = (I + R - 1) / R, nfib = Pg / I;
+    const int items = nch * nfib;
+    for (int it = rs; it < items; it += nrs) {
+      const int ch = it / nfib, fiber = it % nfib;
+      const int aa = fiber % st, bb = fiber / st;
+      const int fbase = aa + st * I * bb;
+      const int j0 = ch * R;
+      float acc[R][C];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < C; ++c) acc[r][c] = 0.f;
+      const float* xp = src + (size_t)fbase * TS + cg * C;
+      const float* mp = MT + j0;
+      for (int i = 0; i < I; ++i) {
+        const float4 x = *reinterpret_cast<const float4*>(xp + (size_t)st * i * TS);
+        const float4 m0 = *reinterpret_cast<const float4*>(mp + i * Ip);
+        const float4 m1 = *reinterpret_cast<const float4*>(mp + i * Ip + 4);
+        const float mv[R] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+        const float xv[C] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+          for (int c = 0; c < C; ++c) acc[r][c] = fmaf(mv[r], xv[c], acc[r][c]);
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+        if (j0 + r < I)
+          *reinterpret_cast<float4*>(dst + (size_t)(fbase + st * (j0 + r)) * TS + cg * C) =
+              make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    }
+    __syncthreads();
+    float* t = src; src = dst; dst = t;
+  }
+  return src;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 template <typename T, int TS>
 __global__ void __launch_bounds__(kThreads, 3)
 transform_kernel(const PassArgs a) {
@@ -66,7 +132,10 @@ transform_kernel(const PassArgs a) {
   const int Pg = (int)p.Pg;
   T* buf0 = reinterpret_cast<T*>(smem_raw);
   T* buf1 = buf0 + (size_t)Pg * TS;
-  T* mats_s = buf1 + (size_t)Pg * TS;
+  // FP32 passes keep a third tile buffer: the next tile streams in (cp.async) while the
+  // current one is transformed
+  T* buf2 = buf1 + (size_t)Pg * TS;
+  T* mats_s = sizeof(T) == 4 ? buf2 + (size_t)Pg * TS : buf2;
 
   // Stage the pass's matrices in shared memory: FP64 row-major I x I; FP32 transposed
   // with rows padded to a multiple of 8 (MT[i][j] = M[j][i], zeros beyond I), so that
@@ -110,6 +179,54 @@ transform_kernel(const PassArgs a) {
   const uint8_t* mk = a.fuse.mask;
   T beta = T(0), step = T(a.fuse.step);
   if (a.fuse_mode != FUSE_NONE) beta = T(a.fuse.scal->beta);
+
+  if constexpr (sizeof(T) == 4) {
+    if (a.vec && a.fuse_mode == FUSE_NONE) {
+      // Plain FP32 pass: three tile buffers.  While tile t is transformed (X <-> Y) and
+      // stored, tile t + gridDim.x streams into P with 16-byte cp.async copies (zero
+      // filled past the end of Sg, which is a multiple of 4 here).
+      float* X = buf0;
+      float* Y = buf1;
+      float* Pf = buf2;
+      const int tv = Pg * TS / 4;
+      auto issue = [&](int64_t tl, float* dst) {
+        const int64_t o = tl / tiles_per_outer;
+        const int64_t s0 = (tl % tiles_per_outer) * TS;
+        const float* gb = gin + o * p.Pg * p.Sg + s0;
+        for (int iv = threadIdx.x; iv < tv; iv += blockDim.x) {
+          const int idx = iv * 4, pp = idx / TS, sc = idx % TS;
+          const bool in = s0 + sc < p.Sg;
+          cp_async16(dst + idx, in ? gb + (int64_t)pp * p.Sg + sc : gin, in ? 16 : 0);
+        }
+      };
+      int64_t tile = blockIdx.x;
+      if (tile < ntiles) issue(tile, X);
+      cp_async_commit();
+      for (; tile < ntiles; tile += gridDim.x) {
+        cp_async_wait_all();
+        __syncthreads();
+        if (tile + gridDim.x < ntiles) issue(tile + gridDim.x, Pf);
+        cp_async_commit();
+        const float* res = modes_f32<TS>(p, mats_s, moff_s, X, Y);
+        const int64_t o = tile / tiles_per_outer;
+        const int64_t s0 = (tile % tiles_per_outer) * TS;
+        float* gb = gout + o * p.Pg * p.Sg + s0;
+        for (int iv = threadIdx.x; iv < tv; iv += blockDim.x) {
+          const int idx = iv * 4, pp = idx / TS, sc = idx % TS;
+          if (s0 + sc < p.Sg)
+            *reinterpret_cast<float4*>(gb + (int64_t)pp * p.Sg + sc) =
+                *reinterpret_cast<const float4*>(res + idx);
+        }
+        __syncthreads();  // X and Y are free again
+        float* t = X;
+        X = Pf;
+        Pf = Y;
+        Y = t;
+      }
+      cp_async_wait_all();
+      return;
+    }
+  }
 
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t o = tile / tiles_per_outer;
@@ -173,51 +290,7 @@ transform_kernel(const PassArgs a) {
     T* src = buf0;
     T* dst = buf1;
     if constexpr (sizeof(T) == 4) {
-      // FP32: a work item is (fiber, 8 consecutive outputs j0..j0+7, 4 consecutive
-      // columns); per input index i one 16-byte load of x (4 columns) and two of the
-      // coefficients feed 32 FMAs.  Items are ordered output chunk first, so the 8 x 4
-      // threads of a warp mostly share j0 (uniform coefficient loads).
-      constexpr int R = 8, C = 4;
-      const int cg = threadIdx.x % (TS / C);
-      const int rs = threadIdx.x / (TS / C);
-      const int nrs = blockDim.x / (TS / C);
-      for (int q = 0; q < p.nm; ++q) {
-        const int I = p.msize[q], st = p.mstride[q], Ip = padded_rows(I);
-        const T* MT = mats_s + moff_s[q];
-        const int nch = (I + R - 1) / R, nfib = Pg / I;
-        const int items = nch * nfib;
-        for (int it = rs; it < items; it += nrs) {
-          const int ch = it / nfib, fiber = it % nfib;
-          const int aa = fiber % st, bb = fiber / st;
-          const int fbase = aa + st * I * bb;
-          const int j0 = ch * R;
-          float acc[R][C];
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc[r][c] = 0.f;
-          const float* xp = src + (size_t)fbase * TS + cg * C;
-          const float* mp = MT + j0;
-          for (int i = 0; i < I; ++i) {
-            const float4 x = *reinterpret_cast<const float4*>(xp + (size_t)st * i * TS);
-            const float4 m0 = *reinterpret_cast<const float4*>(mp + i * Ip);
-            const float4 m1 = *reinterpret_cast<const float4*>(mp + i * Ip + 4);
-            const float mv[R] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
-            const float xv[C] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-              for (int c = 0; c < C; ++c) acc[r][c] = fmaf(mv[r], xv[c], acc[r][c]);
-          }
-#pragma unroll
-          for (int r = 0; r < R; ++r)
-            if (j0 + r < I)
-              *reinterpret_cast<float4*>(dst + (size_t)(fbase + st * (j0 + r)) * TS + cg * C) =
-                  make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-        }
-        __syncthreads();
-        T* t = src; src = dst; dst = t;
-      }
+      src = modes_f32<TS>(p, mats_s, moff_s, src, dst);
     } else
     for (int q = 0; q < p.nm; ++q) {
       const int I = p.msize[q], st = p.mstride[q];
@@ -305,7 +378,7 @@ size_t smem_bytes(const TransformPass& p, int ts) {
   size_t mats = 0;
   for (int q = 0; q < p.nm; ++q)
     mats += (size_t)p.msize[q] * (sizeof(T) == 4 ? padded_rows(p.msize[q]) : p.msize[q]);
-  return (2 * (size_t)p.Pg * ts + mats) * sizeof(T);
+  return ((sizeof(T) == 4 ? 3 : 2) * (size_t)p.Pg * ts + mats) * sizeof(T);
 }
 
 template <typename T, int TS>
