@@ -41,7 +41,8 @@ import numpy as np
 __all__ = [
     "dct_matrix", "cproduct_matrix", "mode_product", "transform", "inverse_transform",
     "slices", "from_slices", "facewise", "product", "identity", "transpose",
-    "svd", "svt", "nuclear_norm", "pga", "pga_objective", "psnr", "rse",
+    "svd", "svt", "truncate", "ranks_and_norms", "nuclear_norm", "pga", "pga_objective",
+    "psnr", "rse",
 ]
 
 
@@ -186,6 +187,49 @@ def svt(A: np.ndarray, tau: float, Ms, return_sigma: bool = False):
     if return_sigma:
         return D, np.stack(sig, axis=1)
     return D
+
+
+def truncate(A: np.ndarray, k: int, Ms) -> np.ndarray:
+    """Rank-k approximation of the Eckart-Young theorem (Sec. 3.2):
+    A_k = U(:, 1:k, ...) *_L S(1:k, 1:k, ...) *_L V(:, 1:k, ...)^T, i.e. per transform
+    domain slice the first k singular triplets of A_hat^p (descending singular values),
+    then L^{-1}.  k >= min(I1, I2) returns A (to rounding), k = 0 the zero tensor."""
+    trailing = A.shape[2:]
+    Ah = slices(transform(A, Ms))
+    Dh = np.empty_like(Ah)
+    for p in range(Ah.shape[2]):
+        u, s, vt = np.linalg.svd(Ah[:, :, p], full_matrices=False)
+        kk = min(int(k), len(s))
+        Dh[:, :, p] = (u[:, :kk] * s[:kk]) @ vt[:kk, :]
+    return inverse_transform(from_slices(Dh, trailing), Ms)
+
+
+def ranks_and_norms(A: np.ndarray, Ms, unit_roundoff: float = 2.0 ** -53) -> dict:
+    """The rank notions and norms of Sec. 3.2 from the per-slice singular values of
+    L(A):
+      multirank    rho_p = rank(L(A)^p)  (Definition "Multirank and average rank")
+      average      mean_p rho_p
+      tubal        card{i : sigma_i(L(A)^p) != 0 for some p}  (Definition and Lemma of
+                   the tubal rank; with descending sigma this is max_p rho_p)
+      spectral     ||bdiag(L(A))||_2 = max_p sigma_1(L(A)^p)  (Proposition on the
+                   spectral norm)
+      nuclear      sum_p sum_i sigma_i(L(A)^p)  (Eq. 24 without the 1/alpha factor;
+                   alpha = 1 for orthonormal transforms)
+    A singular value counts as nonzero when it exceeds max(I1, I2) * u * ||A|| with
+    ||A|| the spectral norm above and u the unit roundoff of the arithmetic being
+    checked: a slice that is zero in exact arithmetic picks up rounding-level singular
+    values from the transforms of the other slices, so the scale is the tensor's, not
+    the slice's."""
+    I1, I2 = A.shape[:2]
+    Ah = slices(transform(A, Ms))
+    P = Ah.shape[2]
+    sig = [np.linalg.svd(Ah[:, :, p], compute_uv=False) for p in range(P)]
+    smax = max(float(s[0]) for s in sig) if P and len(sig[0]) else 0.0
+    tol = max(I1, I2) * unit_roundoff * smax
+    rho = np.array([int(np.sum(s > tol)) if smax > 0 else 0 for s in sig], dtype=np.int64)
+    nuc = float(sum(float(s.sum()) for s in sig))
+    return {"multirank": rho, "average": float(rho.mean()), "tubal": int(rho.max()),
+            "spectral": smax, "nuclear": nuc}
 
 
 def nuclear_norm(A: np.ndarray, Ms) -> float:

@@ -82,6 +82,25 @@ def _pga_momentum_index(mask, obs, tau, step, iters, Ms, tol=0.0, X0=None,
 
 
 _ORIG_PGA = O.pga
+_ORIG_TRUNCATE = O.truncate
+_ORIG_RANKS = O.ranks_and_norms
+
+
+def _truncate_off_by_one(A, k, Ms):  # keeps k + 1 triplets
+    return _ORIG_TRUNCATE(A, k + 1, Ms)
+
+
+def _ranks_slice_relative(A, Ms, unit_roundoff=2.0 ** -53):
+    # tolerance relative to each slice's own largest singular value
+    I1, I2 = A.shape[:2]
+    Ah = O.slices(O.transform(A, Ms))
+    rho = []
+    for p in range(Ah.shape[2]):
+        s = np.linalg.svd(Ah[:, :, p], compute_uv=False)
+        rho.append(int(np.sum(s > max(I1, I2) * unit_roundoff * s[0])) if s[0] > 0 else 0)
+    out = _ORIG_RANKS(A, Ms, unit_roundoff)
+    out["multirank"] = np.array(rho)
+    return out
 
 MUTATIONS = [
     ("dct_matrix", _dct_delta_ij, [pins.test_dct_matrix_closed_forms_and_scipy]),
@@ -95,6 +114,8 @@ MUTATIONS = [
     ("svt", _svt_unclamped, [pins.test_svt_special_cases]),
     ("pga", _pga_wrong_gradient_sign, [pins.test_pga_first_iterates_and_momentum_schedule]),
     ("pga", _pga_momentum_index, [pins.test_pga_first_iterates_and_momentum_schedule]),
+    ("truncate", _truncate_off_by_one, [pins.test_truncate_is_the_eckart_young_product]),
+    ("ranks_and_norms", _ranks_slice_relative, [pins.test_ranks_and_norms_on_prescribed_ranks]),
 ]
 
 

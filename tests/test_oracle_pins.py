@@ -246,6 +246,56 @@ def test_eckart_young_dct():
         assert np.linalg.norm(A - O.product(X, Y, Ms)) ** 2 >= err2 - 1e-10
 
 
+def test_truncate_is_the_eckart_young_product():
+    """O.truncate(A, k) equals the theorem's U(:,1:k) *_L S(1:k,1:k) *_L V(:,1:k)^T built
+    with *_L-products from the full *_L-SVD (a different route: products and
+    transposes of the SVD factors in the original domain), for DCT and a general
+    invertible L; k = 0 gives zero, k >= min(I1, I2) gives A; and for I3 = 1 with the
+    identity transform it is LAPACK's matrix rank-k truncation."""
+    rng = np.random.default_rng(21)
+    trailing = (3, 2)
+    for Ms in ([O.dct_matrix(n) for n in trailing],
+               [rng.standard_normal((n, n)) + 3 * np.eye(n) for n in trailing]):
+        A = rand(rng, 6, 5, *trailing)
+        U, S, V, _ = O.svd(A, Ms)
+        for k in (1, 2, 4):
+            Ak = O.product(O.product(U[:, :k], S[:k, :k], Ms), O.transpose(V[:, :k], Ms), Ms)
+            assert np.linalg.norm(O.truncate(A, k, Ms) - Ak) <= 1e-11 * np.linalg.norm(A)
+        assert np.linalg.norm(O.truncate(A, 0, Ms)) == 0.0
+        assert np.linalg.norm(O.truncate(A, 7, Ms) - A) <= 1e-12 * np.linalg.norm(A)
+    M = rng.standard_normal((7, 5))
+    u, s, vt = np.linalg.svd(M, full_matrices=False)
+    got = O.truncate(M[:, :, None], 2, [np.eye(1)])[:, :, 0]
+    assert np.linalg.norm(got - (u[:, :2] * s[:2]) @ vt[:2]) <= 1e-13 * np.linalg.norm(M)
+
+
+def test_ranks_and_norms_on_prescribed_ranks():
+    """Tensors built in the transform domain with prescribed slice ranks r_p
+    (L(A)^p = X_p Y_p, X_p I1 x r_p, Y_p r_p x I2): the multirank is r, the average
+    rank mean(r), the tubal rank max(r) (Lemma of the tubal rank); with I3 = 1 and the
+    identity transform the spectral and nuclear norms are LAPACK's matrix 2-norm and
+    nuclear norm."""
+    rng = np.random.default_rng(22)
+    trailing = (3, 2)
+    for Ms in ([O.dct_matrix(n) for n in trailing],
+               [rng.standard_normal((n, n)) + 3 * np.eye(n) for n in trailing]):
+        r = [2, 0, 5, 1, 3, 4]
+        Ah = np.zeros((8, 6, 6))
+        for p, rp in enumerate(r):
+            Ah[:, :, p] = rng.standard_normal((8, rp)) @ rng.standard_normal((rp, 6))
+        A = O.inverse_transform(O.from_slices(Ah, trailing), Ms)
+        out = O.ranks_and_norms(A, Ms)
+        assert list(out["multirank"]) == r
+        assert out["tubal"] == 5 and out["average"] == sum(r) / 6
+        sig = [np.linalg.svd(Ah[:, :, p], compute_uv=False) for p in range(6)]
+        assert abs(out["spectral"] - max(x[0] for x in sig)) <= 1e-9 * out["spectral"]
+    M = rng.standard_normal((7, 5))
+    out = O.ranks_and_norms(M[:, :, None], [np.eye(1)])
+    assert abs(out["spectral"] - np.linalg.norm(M, 2)) <= 1e-13 * np.linalg.norm(M, 2)
+    assert abs(out["nuclear"] - np.linalg.norm(M, "nuc")) <= 1e-13 * np.linalg.norm(M, "nuc")
+    assert out["tubal"] == 5 and list(out["multirank"]) == [5]
+
+
 def test_svt_special_cases():
     rng = np.random.default_rng(14)
     trailing = (4,)
