@@ -80,7 +80,9 @@ typedef enum {
   LT_OP_PRODUCT = 2,
   LT_OP_SVD = 3,
   LT_OP_SVT = 4,
-  LT_OP_PGA = 5
+  LT_OP_PGA = 5,
+  LT_OP_TRUNCATE = 6,
+  LT_OP_NORMS = 7
 } lt_op;
 
 typedef enum {
@@ -211,6 +213,29 @@ LT_API lt_status lt_svd(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, void*
  * unscaled in the transform domain.  tau >= 0.  D may alias A. */
 LT_API lt_status lt_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau, void* D,
                  void* ws, size_t ws_bytes, void* stream);
+
+/* Rank-k approximation of the Eckart-Young theorem (Sec. 3.2):
+ *   A_k = U(:, 1:k, ...) *_L S(1:k, 1:k, ...) *_L V(:, 1:k, ...)^T,
+ * i.e. per transform-domain slice the k largest singular triplets of L(A)^p (ties
+ * broken by column order; zero singular values are never kept), then L^{-1}.  k >= 0;
+ * k >= min(I1, I2) returns A to rounding, k = 0 zeros.  A_k may alias A.  Workspace:
+ * lt_workspace_size(LT_OP_TRUNCATE). */
+LT_API lt_status lt_truncate(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, int64_t k,
+                             void* A_k, void* ws, size_t ws_bytes, void* stream);
+
+/* Norms and ranks of Sec. 3.2 from the singular values sigma_i^p of every slice L(A)^p:
+ *   out[0] = sum_p sum_i sigma_i^p   (nuclear norm, Eq. 24 / Theorem 21, without the
+ *                                     1/alpha factor: alpha = 1 for orthonormal L)
+ *   out[1] = max_p sigma_1^p         (spectral norm ||bdiag(L(A))||, proposition of
+ *                                     Sec. 3.2)
+ *   out[2] = tubal rank = max_p rho_p (definition of the tubal rank and its lemma)
+ *   out[3] = average rank = mean_p rho_p (definition of multirank and average rank)
+ *   multirank[p] = rho_p = rank(L(A)^p), nullable
+ * A singular value counts as nonzero above max(I1, I2) * u * out[1] (u = 2^-53 for
+ * LT_FP64, 2^-24 otherwise).  out: device, 4 doubles; multirank: device, P int32.
+ * Workspace: lt_workspace_size(LT_OP_NORMS). */
+LT_API lt_status lt_norms(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double* out,
+                          int32_t* multirank, void* ws, size_t ws_bytes, void* stream);
 
 /* Checkpoint of a PGA run (Algorithm 5): X^{k-1} (caller-owned device buffer of the
  * problem's size), t_{k-1}, t_k and k.  With k == 0 the run starts from X^0 = X^1 =

@@ -160,7 +160,9 @@ cudaError_t run_jacobi(Ctx& c, const lt::JacobiPlan& jp, lt::JacobiIO io, cudaSt
   cudaError_t e = lt::launch_jacobi(c, jp, io, st);
   // bytes: read the slices, re-read them for the reconstruction, write the result
   const double n = (double)jp.I1 * jp.I2 * c.P * c.elem;
-  sc.done(1, 0.0, jp.mode == lt::JAC_SVT ? 3 * n : 2 * n);
+  // bytes: read the slices (SVT and truncation re-read them for the reconstruction
+  // and write the result; the SVD writes its factors; the singular values alone read)
+  sc.done(1, 0.0, jp.mode == lt::JAC_SVD ? 2 * n : (jp.mode == lt::JAC_SIGMA ? n : 3 * n));
   return e;
 }
 
@@ -446,6 +448,21 @@ lt_status lt_workspace_size(lt_ctx ctx, lt_op op, int64_t I1, int64_t I2, int64_
       *out = align256(jp.ws_bytes);
       return LT_OK;
     }
+    case LT_OP_TRUNCATE: {
+      lt::JacobiPlan jp;
+      s = lt::plan_jacobi(c, lt::JAC_TRUNC, I1, I2, &jp);
+      if (s != LT_OK) return s;
+      *out = align256(jp.ws_bytes);
+      return LT_OK;
+    }
+    case LT_OP_NORMS: {
+      lt::JacobiPlan jp;
+      s = lt::plan_jacobi(c, lt::JAC_SIGMA, I1, I2, &jp);
+      if (s != LT_OK) return s;
+      *out = align256((size_t)I1 * I2 * c.P * c.elem) + align256(jp.ws_bytes) +
+             align256((size_t)std::min(I1, I2) * c.P * c.elem);
+      return LT_OK;
+    }
     case LT_OP_PGA: {
       PgaLayout L;
       s = pga_layout(c, I1, I2, &L);
@@ -573,6 +590,67 @@ lt_status lt_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau, 
   cudaError_t e = run_transform(c, pf, I1 * I2, A, D, st);
   if (e == cudaSuccess) e = run_jacobi(c, jp, io, st);
   if (e == cudaSuccess) e = run_transform(c, pi, I1 * I2, D, D, st);
+  return cuda_status(e);
+}
+
+lt_status lt_truncate(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, int64_t k, void* A_k,
+                      void* ws, size_t ws_bytes, void* stream) {
+  if (check_ctx(ctx) != LT_OK || !A || !A_k || k < 0) return LT_ERR_ARG;
+  lt_status s = check_dims(I1, I2);
+  if (s != LT_OK) return s;
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  size_t need = 0;
+  if ((s = lt_workspace_size(ctx, LT_OP_TRUNCATE, I1, I2, 0, &need)) != LT_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, need)) != LT_OK) return s;
+  lt::JacobiPlan jp;
+  lt::TransformPlan pf, pi;
+  if ((s = lt::plan_jacobi(c, lt::JAC_TRUNC, I1, I2, &jp)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, I1 * I2, false, &pf)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, I1 * I2, true, &pi)) != LT_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  lt::JacobiIO io;
+  io.A = A_k;
+  io.D = A_k;
+  io.trunc_k = k;
+  io.scratch = ws;
+  cudaError_t e = run_transform(c, pf, I1 * I2, A, A_k, st);
+  if (e == cudaSuccess) e = run_jacobi(c, jp, io, st);
+  if (e == cudaSuccess) e = run_transform(c, pi, I1 * I2, A_k, A_k, st);
+  return cuda_status(e);
+}
+
+lt_status lt_norms(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double* out,
+                   int32_t* multirank, void* ws, size_t ws_bytes, void* stream) {
+  if (check_ctx(ctx) != LT_OK || !A || !out) return LT_ERR_ARG;
+  lt_status s = check_dims(I1, I2);
+  if (s != LT_OK) return s;
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  size_t need = 0;
+  if ((s = lt_workspace_size(ctx, LT_OP_NORMS, I1, I2, 0, &need)) != LT_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, need)) != LT_OK) return s;
+  lt::JacobiPlan jp;
+  lt::TransformPlan pf;
+  if ((s = lt::plan_jacobi(c, lt::JAC_SIGMA, I1, I2, &jp)) != LT_OK) return s;
+  if ((s = lt::plan_transform(c, I1 * I2, false, &pf)) != LT_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  void* Ah = w;
+  void* scratch = w + align256((size_t)I1 * I2 * c.P * c.elem);
+  void* sigma = static_cast<unsigned char*>(scratch) + align256(jp.ws_bytes);
+  lt::JacobiIO io;
+  io.A = Ah;
+  io.D = nullptr;
+  io.sigma = sigma;
+  io.scratch = scratch;
+  cudaError_t e = run_transform(c, pf, I1 * I2, A, Ah, st);
+  if (e == cudaSuccess) e = run_jacobi(c, jp, io, st);
+  if (e == cudaSuccess) {
+    Scope sc(c, st, LT_K_AUX);
+    const double u = c.elem == 8 ? 0x1p-53 : 0x1p-24;
+    e = lt::launch_norms_finish(sigma, c.elem, c.P, (int)std::min(I1, I2),
+                                (double)std::max(I1, I2) * u, out, multirank, st);
+    sc.done(1, 0.0, (double)std::min(I1, I2) * c.P * c.elem);
+  }
   return cuda_status(e);
 }
 

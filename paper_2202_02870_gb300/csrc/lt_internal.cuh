@@ -155,7 +155,9 @@ cudaError_t launch_tc_gemm(const TcGemm& g, int forced_bn, int32_t* status, cuda
 // ----------------------------------------------------------------------------------
 // Jacobi SVD / SVT (kernel J), one CTA per slice.
 // ----------------------------------------------------------------------------------
-enum JacobiMode { JAC_SVT = 0, JAC_SVD = 1 };
+// JAC_SVT, JAC_TRUNC and JAC_SIGMA run the QR-preconditioned SVT kernel: shrink by tau,
+// keep the trunc_k largest singular triplets, or only write the singular values.
+enum JacobiMode { JAC_SVT = 0, JAC_SVD = 1, JAC_TRUNC = 2, JAC_SIGMA = 3 };
 
 struct JacobiPlan {
   int mode = JAC_SVT;
@@ -187,6 +189,7 @@ struct JacobiIO {
   void* V = nullptr;
   void* sigma = nullptr;    // optional, min(I1,I2) per slice
   double tau = 0.0;         // SVT threshold (host value)
+  int64_t trunc_k = 0;      // JAC_TRUNC: singular triplets kept per slice
   const PgaScalars* scal = nullptr;  // PGA: skip when done
   void* scratch = nullptr;  // jp.ws_bytes
   SliceInfo* info = nullptr;
@@ -206,6 +209,12 @@ cudaError_t launch_pga_finish(PgaScalars* scal, const double* partials, int rows
                               const SliceInfo* info, int64_t P, double tau, int objective,
                               int32_t* ctx_status, cudaStream_t st);
 cudaError_t launch_copy_bytes(void* dst, const void* src, size_t bytes, cudaStream_t st);
+// Norms and ranks from the per-slice singular values sigma (n per slice, context
+// precision): out[0] = sum of all sigma, out[1] = max sigma, out[2] = tubal rank,
+// out[3] = average rank; multirank[p] (nullable) = count of sigma of slice p above
+// max(I1, I2) * u * max sigma.
+cudaError_t launch_norms_finish(const void* sigma, int elem, int64_t P, int n, double rank_tol,
+                                double* out, int32_t* multirank, cudaStream_t st);
 cudaError_t launch_select_result(const PgaScalars* scal, void* x_user, const void* x_alt,
                                  void* x_prev_out, size_t bytes, cudaStream_t st);
 

@@ -416,7 +416,7 @@ cudaError_t launch_t(const JArgs& a, int grid, cudaStream_t st) {
 }
 
 int jacobi_grid(const Ctx& c, const JacobiPlan& jp) {
-  if (jp.w_in_smem && jp.mode == JAC_SVT) return (int)std::min<int64_t>(jp.P, 1 << 20);
+  if (jp.w_in_smem && jp.mode != JAC_SVD) return (int)std::min<int64_t>(jp.P, 1 << 20);
   // global regions are per CTA: bound the grid by what can be resident
   return (int)std::max<int64_t>(1, std::min<int64_t>(jp.P, (int64_t)c.sms * 2));
 }
@@ -506,7 +506,7 @@ lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan
   jp.threads = kJThreads;
   jp.w_in_smem = true;
   size_t need;
-  if (mode == JAC_SVT) {
+  if (mode != JAC_SVD) {
     // QR-preconditioned kernel: Jacobi on the n x n factor R^T, G lanes per column
     // pair holding E rows each, leading dimension >= max(m, G E) and odd (conflict-free
     // transposed stores); as many warps as the pairs of a round need, within the cap.
@@ -572,12 +572,12 @@ cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io
   // slices) and the momentum of PGA amplifies per-call errors about tenfold; below ~4 u
   // the rounding of the FP32 dot products keeps small slices from converging
   const double u = c.elem == 8 ? DBL_EPSILON / 2 : FLT_EPSILON / 2;
-  const double rows = jp.mode == JAC_SVT ? jp.n : jp.m;
+  const double rows = jp.mode != JAC_SVD ? jp.n : jp.m;
   a.tol = c.jacobi_tol > 0 ? c.jacobi_tol
                            : (c.elem == 8 ? rows * u : std::max(std::sqrt(rows) / 8.0, 4.0) * u);
   a.status = c.d_status;
   const int grid = jacobi_grid(c, jp);
-  if (jp.mode == JAC_SVT) {
+  if (jp.mode != JAC_SVD) {
     // try the translation units in turn; each returns cudaErrorNotSupported for shapes
     // it does not hold
     using L = cudaError_t (*)(const JArgs&, int, cudaStream_t);

@@ -197,7 +197,7 @@ jacobi_svt_kernel(const JArgs a) {
   long long tqr[4];  // QR sub-phase totals (thread 0, profiling only)
   for (int64_t slice = blockIdx.x; slice < jp.P; slice += gridDim.x) {
     const T* A = Ain + slice * I1 * I2;
-    T* D = reinterpret_cast<T*>(a.io.D) + slice * I1 * I2;
+    T* D = a.io.D ? reinterpret_cast<T*>(a.io.D) + slice * I1 * I2 : nullptr;
     if (a.io.phases && threadIdx.x == 0) tph[0] = clock64();
     // ---- load B; zero the padding rows and column
     if (!jp.transposed) {
@@ -237,7 +237,8 @@ jacobi_svt_kernel(const JArgs a) {
     const T sc = pow2_scale(from_abs_bits<T>(s_maxbits));
     if (sc != T(1))
       for (int idx = threadIdx.x; idx < ld * np; idx += blockDim.x) W[idx] *= sc;
-    const T tau = tau_in * sc;
+    // truncation keeps sigma unshrunk: g_i = 1 / sigma_i^2 is the SVT rule at tau = 0
+    const T tau = jp.mode == JAC_SVT ? tau_in * sc : T(0);
     __syncthreads();
 
     if (a.io.phases && threadIdx.x == 0) tph[1] = clock64();
@@ -635,7 +636,24 @@ jacobi_svt_kernel(const JArgs a) {
     __syncthreads();
     if (a.io.phases && threadIdx.x == 0) tph[3] = clock64();
 
-    // ---- 3. shrink and reconstruct
+    // ---- 3. shrink (or truncate, or report sigma) and reconstruct
+    if (jp.mode == JAC_TRUNC) {
+      // keep column c when fewer than trunc_k columns have a larger norm (ties by
+      // index) and its norm is nonzero; the flag goes to ref[], free after the QR
+      for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const T sc2 = nrm2[c];
+        int64_t rank = 0;
+        for (int c2 = 0; c2 < n; ++c2) {
+          const T s2 = nrm2[c2];
+          rank += (s2 > sc2 || (s2 == sc2 && c2 < c)) ? 1 : 0;
+        }
+        ref[c] = (rank < a.io.trunc_k && sc2 > T(0)) ? T(1) : T(0);
+      }
+      __syncthreads();
+    }
+    if (a.io.sigma)
+      for (int c = threadIdx.x; c < n; c += blockDim.x)
+        reinterpret_cast<T*>(a.io.sigma)[slice * n + c] = sqrt(nrm2[c]) / sc;
     if (threadIdx.x == 0) {
       int st = 0, k = 0;
       T nuc = T(0);
@@ -644,7 +662,8 @@ jacobi_svt_kernel(const JArgs a) {
         const T s2 = nrm2[c];
         if (!isfinite(s2)) st |= LT_DEV_NONFINITE;
         const T sg = sqrt(s2);
-        if (sg > tau) {
+        const bool keep = jp.mode == JAC_SVT ? sg > tau : (jp.mode == JAC_TRUNC && ref[c] != T(0));
+        if (keep) {
           list[k++] = c;
           nuc += sg - tau;
         }
@@ -677,7 +696,7 @@ jacobi_svt_kernel(const JArgs a) {
     if (a.io.phases && threadIdx.x == 0) tph[5] = clock64();
     // a warp per row of B P, lane l holding columns l, l+32, ... (ER per lane)
     constexpr int ER = (G * E + 31) / 32;
-    const int rows_iter = (m + nwarps - 1) / nwarps;
+    const int rows_iter = D != nullptr ? (m + nwarps - 1) / nwarps : 0;
     for (int it = 0; it < rows_iter; ++it) {
       const int r = it * nwarps + warp;
       const bool active = r < m;

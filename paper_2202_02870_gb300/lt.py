@@ -24,7 +24,8 @@ STATUS = {0: "LT_OK", -1: "LT_ERR_ARG", -2: "LT_ERR_SHAPE", -3: "LT_ERR_SINGULAR
           -7: "LT_ERR_CUDA", -8: "LT_ERR_WORKSPACE"}
 LT_DEV_NOCONV, LT_DEV_NONFINITE, LT_DEV_TIMEOUT = 1, 2, 4
 LT_FP64, LT_FP32, LT_MIXED = 0, 1, 2
-LT_OP_TRANSFORM, LT_OP_INVERSE, LT_OP_PRODUCT, LT_OP_SVD, LT_OP_SVT, LT_OP_PGA = range(6)
+(LT_OP_TRANSFORM, LT_OP_INVERSE, LT_OP_PRODUCT, LT_OP_SVD, LT_OP_SVT, LT_OP_PGA, LT_OP_TRUNCATE,
+ LT_OP_NORMS) = range(8)
 (LT_OPT_MAX_SWEEPS, LT_OPT_JACOBI_TOL, LT_OPT_OBJECTIVE, LT_OPT_PROFILE, LT_OPT_JACOBI_GROUP,
  LT_OPT_JACOBI_BLOCK, LT_OPT_TC_MODE_MIN, LT_OPT_TC_TILE_N) = 0, 1, 2, 3, 4, 5, 6, 7
 LT_K_TRANSFORM, LT_K_JACOBI, LT_K_GEMM, LT_K_AUX = 0, 1, 2, 3
@@ -79,6 +80,8 @@ SIGNATURES = {
                                           C.POINTER(C.c_double), _i64, C.POINTER(C.c_void_p),
                                           C.POINTER(lt_pga_report), _vp, _sz, _vp]),
     "lt_product_noalloc": (C.c_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp]),
+    "lt_truncate": (C.c_int, [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "lt_norms": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
     "lt_ctx_get_stats": (C.c_int, [_vp, C.POINTER(lt_stats), C.c_int]),
     "lt_last_device_status": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "lt_status_string": (C.c_char_p, [C.c_int]),
@@ -280,6 +283,33 @@ def lt_svt(ctx, A, tau, D, ws=None, stream=None):
     _check("lt_svt", lib().lt_svt(ctx.handle, I1, I2, _ptr(A), float(tau), _ptr(D),
                                   _ptr(ws), nb, _stream(stream)))
     return D
+
+
+def lt_truncate(ctx, A, k, A_k, ws=None, stream=None):
+    _require(A, ctx, "A"); _require(A_k, ctx, "A_k")
+    I1, I2 = _dims(A)
+    need = lt_workspace_size(ctx, LT_OP_TRUNCATE, I1, I2)
+    ws, nb = _workspace(ctx, need, A.device, ws)
+    _check("lt_truncate", lib().lt_truncate(ctx.handle, I1, I2, _ptr(A), int(k), _ptr(A_k),
+                                            _ptr(ws), nb, _stream(stream)))
+    return A_k
+
+
+def lt_norms(ctx, A, out, multirank=None, ws=None, stream=None):
+    """out: CUDA float64 tensor of 4 (nuclear sum, spectral, tubal rank, average rank);
+    multirank: CUDA int32 tensor of P or None."""
+    _require(A, ctx, "A")
+    import torch
+    if not out.is_cuda or out.dtype != torch.float64 or out.numel() < 4:
+        raise ValueError("out: expected a CUDA float64 tensor of 4 elements")
+    if multirank is not None and (not multirank.is_cuda or multirank.dtype != torch.int32):
+        raise ValueError("multirank: expected a CUDA int32 tensor")
+    I1, I2 = _dims(A)
+    need = lt_workspace_size(ctx, LT_OP_NORMS, I1, I2)
+    ws, nb = _workspace(ctx, need, A.device, ws)
+    _check("lt_norms", lib().lt_norms(ctx.handle, I1, I2, _ptr(A), _ptr(out), _ptr(multirank),
+                                      _ptr(ws), nb, _stream(stream)))
+    return out
 
 
 def lt_pga_complete(ctx, mask, obs, tau, step, iters, X, tol=0.0, state=None, report=None,
