@@ -109,8 +109,15 @@ typedef enum {
                                 on the tensor cores; mode 3 and smaller modes are applied
                                 by the SIMT transform kernel (fused passes); 0 = no
                                 tensor-core transform passes */
-  LT_OPT_TC_TILE_N = 7       /* LT_MIXED: output tile width of the tensor-core kernel
+  LT_OPT_TC_TILE_N = 7,      /* LT_MIXED: output tile width of the tensor-core kernel
                                 (32, 64, 128 or 256); 0 (default) = chosen per call */
+  LT_OPT_MU0 = 8,            /* PGA continuation (Algorithm 5, mu_{k+1} = max(nu mu_k,
+                                mu_bar)): mu_0 > 0 turns it on, with mu_bar = the tau
+                                argument of lt_pga_complete; iteration k (counted from
+                                the start of the run, checkpoints included) thresholds at
+                                step * max(nu^k mu_0, tau).  0 (default) = off, fixed tau.
+                                Not available in lt_pga_complete_batched (LT_ERR_ARG). */
+  LT_OPT_NU = 9              /* PGA continuation decay nu, 0 < nu <= 1 (default 0.9) */
 } lt_option;
 
 /* Kernel families counted by lt_ctx_get_stats. */

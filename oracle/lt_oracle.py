@@ -251,8 +251,11 @@ def pga_objective(X, mask, obs, tau, Ms) -> float:
 
 
 def pga(mask, obs, tau, step, iters, Ms, tol=0.0, X0=None, momentum=True,
-        objective=False):
-    """Tensor completion by PGA, Algorithm 5 with fixed mu = tau (continuation off):
+        objective=False, mu0=0.0, nu=0.9):
+    """Tensor completion by PGA, Algorithm 5.  With mu0 = 0 (default) the threshold is
+    the fixed mu = tau; with mu0 > 0 it follows the continuation of Algorithm 5,
+    mu_{k+1} = max(nu mu_k, mu_bar), read with mu_bar = tau: iteration k (0-based)
+    thresholds at step * max(nu^k mu0, tau).
 
         X^0 = X^1 = X0 (zeros by default), t_0 = t_1 = 1
         repeat:  Y^k = X^k + ((t_{k-1} - 1) / t_k) (X^k - X^{k-1})      (Eq. 52)
@@ -278,7 +281,8 @@ def pga(mask, obs, tau, step, iters, Ms, tol=0.0, X0=None, momentum=True,
         beta = (t_prev - 1.0) / t if momentum else 0.0
         Y = X + beta * (X - X_prev)
         G = Y - step * m * (Y - obs)
-        X_new = svt(G, step * tau, Ms)
+        mu = max(nu ** k_done * mu0, tau) if mu0 > 0 else tau
+        X_new = svt(G, step * mu, Ms)
         nx = float(np.linalg.norm(X_new))
         ny = float(np.linalg.norm(Y - X_new))
         r = ny / nx if nx > 0 else float(np.linalg.norm(Y))

@@ -406,6 +406,14 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
       if (!(value >= 0 && value <= 4096) || value != std::floor(value)) return LT_ERR_ARG;
       c->tc_mode_min = (int)value;
       return LT_OK;
+    case LT_OPT_MU0:
+      if (!(value >= 0.0) || !std::isfinite(value)) return LT_ERR_ARG;
+      c->mu0 = value;
+      return LT_OK;
+    case LT_OPT_NU:
+      if (!(value > 0.0 && value <= 1.0)) return LT_ERR_ARG;
+      c->nu = value;
+      return LT_OK;
     case LT_OPT_TC_TILE_N:
       if (!(value == 0 || value == 32 || value == 64 || value == 128 || value == 256))
         return LT_ERR_ARG;
@@ -811,7 +819,13 @@ lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8_t* mas
   if (s != LT_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e = pga_begin(r, state, tol, st);
-  for (int64_t j = 0; j < iters && e == cudaSuccess; ++j) e = pga_iteration(r, j, st, true);
+  const int64_t k0 = (state && state->k > 0) ? state->k : 0;
+  for (int64_t j = 0; j < iters && e == cudaSuccess; ++j) {
+    // continuation (Algorithm 5, mu_{k+1} = max(nu mu_k, mu_bar) with mu_bar = tau):
+    // iteration k thresholds at step * max(nu^k mu_0, tau); off (mu_0 = 0): step * tau
+    if (c.mu0 > 0.0) r.io.tau = step * std::max(std::pow(c.nu, (double)(k0 + j)) * c.mu0, tau);
+    e = pga_iteration(r, j, st, true);
+  }
   if (e == cudaSuccess) e = pga_end(r, state, report, st);
   return cuda_status(e);
 }
@@ -846,6 +860,7 @@ lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const int64_t* 
     if (!ctxs[i] || !mask[i] || !obs[i] || !X[i]) return LT_ERR_ARG;
     if (!(tau[i] >= 0.0) || !std::isfinite(tau[i]) || !(step[i] > 0.0) || !std::isfinite(step[i]))
       return LT_ERR_ARG;
+    if (reinterpret_cast<Ctx*>(ctxs[i])->mu0 > 0.0) return LT_ERR_ARG;  // one graph, fixed tau
     if (reinterpret_cast<Ctx*>(ctxs[i])->prec != reinterpret_cast<Ctx*>(ctxs[0])->prec)
       return LT_ERR_ARG;
     for (int j = 0; j < i; ++j)  // one context per problem: report staging is per context

@@ -40,6 +40,8 @@ struct Ctx {
   int tc_mode_min = 64;               // LT_MIXED: modes of at least this size (and not
                                       // mode 3) run as tensor-core passes; 0 = never
   int tc_tile_n = 0;                  // LT_MIXED: forced tensor-core tile width (0 = auto)
+  double mu0 = 0.0;                   // PGA continuation: mu_0 (0 = off)
+  double nu = 0.9;                    // PGA continuation: decay of mu
   mutable int64_t tc_launches = 0;    // tensor-core kernel launches (lt_ctx_get_stats)
   // LT_MIXED: the transform matrices as tensor-core B operands, B(k, n) = M(n, k) at
   // k + n * ld (ld = I rounded up to 4, zero padded), each at a 16-byte aligned offset.

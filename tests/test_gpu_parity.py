@@ -314,6 +314,47 @@ def test_pga_step_and_tolerance_stop():
     assert rel(from_dev(X, obs.shape), ref) <= 1e-12
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_pga_continuation(prec):
+    """Algorithm 5 with continuation (LT_OPT_MU0 = nu ||M||_F, the paper's choice, and
+    nu = 0.9; mu_bar = tau): 40 iterations against the oracle, and a 20 + 20 resume
+    through the checkpoint equal to the single run bit for bit (the schedule counts
+    iterations from the start of the run)."""
+    c = synth.completion_case(12, 24, 20, (3, 4), rank=3, rho=0.4)
+    tr = [("dct", 3), ("dct", 4)]
+    Ms = oracle_mats(tr)
+    X0 = O.product(c["U"], O.transpose(c["V"], Ms), Ms)
+    obs = c["mask"] * (X0 + c["noise"])
+    mu0 = 0.9 * float(np.linalg.norm(obs))
+    ref, _ = O.pga(c["mask"], obs, 0.3, 1.0, 40, Ms, mu0=mu0, nu=0.9)
+    dt = dtype_of(prec)
+    ctx = make_ctx(tr, prec)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_MU0, mu0)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_NU, 0.9)
+    mask_d, obs_d = to_dev(c["mask"]), to_dev(obs, dt)
+    X = torch.zeros((4, 3, 20, 24), dtype=dt, device="cuda")
+    lt.lt_pga_complete(ctx, mask_d, obs_d, 0.3, 1.0, 40, X)
+    torch.cuda.synchronize()
+    assert rel(from_dev(X, obs.shape), ref) <= TOL[prec]
+    Xr = torch.zeros_like(X)
+    Xp = torch.empty_like(X)
+    state = lt.lt_pga_state(Xp.data_ptr(), 0.0, 0.0, 0)
+    lt.lt_pga_complete(ctx, mask_d, obs_d, 0.3, 1.0, 20, Xr, state=state)
+    torch.cuda.synchronize()
+    lt.lt_pga_complete(ctx, mask_d, obs_d, 0.3, 1.0, 20, Xr, state=state)
+    torch.cuda.synchronize()
+    assert torch.equal(Xr, X)
+    # one graph per batch: continuation is refused there, nothing enqueued
+    with pytest.raises(lt.LtError):
+        lt.lt_pga_complete_batched([ctx], [mask_d], [obs_d], [0.3], [1.0], 2, [Xr])
+    for bad in (-1.0, float("nan")):
+        with pytest.raises(lt.LtError):
+            lt.lt_ctx_set_option(ctx, lt.LT_OPT_MU0, bad)
+    for bad in (0.0, 1.5):
+        with pytest.raises(lt.LtError):
+            lt.lt_ctx_set_option(ctx, lt.LT_OPT_NU, bad)
+
+
 def test_pga_resume_is_bitwise():
     """50 + 50 iterations through the checkpoint state equal 100 in one call, bit for bit
     (fixed-order reductions)."""

@@ -86,6 +86,13 @@ _ORIG_TRUNCATE = O.truncate
 _ORIG_RANKS = O.ranks_and_norms
 
 
+def _pga_continuation_late(mask, obs, tau, step, iters, Ms, tol=0.0, X0=None,
+                           momentum=True, objective=False, mu0=0.0, nu=0.9):
+    # the schedule starts at nu * mu0 instead of mu0
+    return _ORIG_PGA(mask, obs, tau, step, iters, Ms, tol, X0, momentum, objective,
+                     mu0 * nu, nu)
+
+
 def _truncate_off_by_one(A, k, Ms):  # keeps k + 1 triplets
     return _ORIG_TRUNCATE(A, k + 1, Ms)
 
@@ -114,6 +121,7 @@ MUTATIONS = [
     ("svt", _svt_unclamped, [pins.test_svt_special_cases]),
     ("pga", _pga_wrong_gradient_sign, [pins.test_pga_first_iterates_and_momentum_schedule]),
     ("pga", _pga_momentum_index, [pins.test_pga_first_iterates_and_momentum_schedule]),
+    ("pga", _pga_continuation_late, [pins.test_pga_continuation_schedule_and_limit]),
     ("truncate", _truncate_off_by_one, [pins.test_truncate_is_the_eckart_young_product]),
     ("ranks_and_norms", _ranks_slice_relative, [pins.test_ranks_and_norms_on_prescribed_ranks]),
 ]

@@ -399,6 +399,37 @@ def test_pga_ista_monotone_and_limit_is_optimal():
         assert fk - Fstar <= 2 * np.linalg.norm(Xf) ** 2 / (k + 1) ** 2 + 1e-9
 
 
+def test_pga_continuation_schedule_and_limit():
+    """Continuation of Algorithm 5 (mu_{k+1} = max(nu mu_k, mu_bar), mu_bar = tau):
+    mu_0 <= tau is the fixed-tau run; nu = 1 is the fixed run at mu_0; the first iterate
+    is D_{step mu_0}(step P_Omega(M)) (X^0 = 0); and the limit is a minimiser of the
+    tau problem: its objective beats random perturbations and equals the fixed-tau
+    limit's or lies below it (continuation reaches the optimum faster; convex
+    optimality)."""
+    X, mask, obs, Ms = small_completion(rho=0.6)
+    tau = 0.05
+    a, _ = O.pga(mask, obs, tau, 1.0, 12, Ms)
+    b, _ = O.pga(mask, obs, tau, 1.0, 12, Ms, mu0=tau, nu=0.5)
+    assert np.array_equal(a, b)
+    c, _ = O.pga(mask, obs, 2.0, 1.0, 12, Ms)
+    d, _ = O.pga(mask, obs, tau, 1.0, 12, Ms, mu0=2.0, nu=1.0)
+    assert np.array_equal(c, d)
+    x1, _ = O.pga(mask, obs, tau, 0.8, 1, Ms, mu0=3.0, nu=0.7)
+    m = mask.astype(float)
+    assert np.linalg.norm(x1 - O.svt(0.8 * m * obs, 0.8 * 3.0, Ms)) <= 1e-13 * np.linalg.norm(x1)
+    mu0 = 0.9 * float(np.linalg.norm(m * obs))     # the paper's choice nu ||M||_F
+    Xc, infoc = O.pga(mask, obs, tau, 1.0, 400, Ms, mu0=mu0, nu=0.9, objective=True)
+    Xf, infof = O.pga(mask, obs, tau, 1.0, 400, Ms, objective=True)
+    Fc = infoc["objective"][-1]
+    assert Fc <= infof["objective"][-1] + 1e-9 * abs(Fc)
+    assert infof["objective"][-1] - Fc <= 1e-5 * abs(Fc)
+    assert infoc["objective"][0] > infof["objective"][0]   # early iterates over-shrink
+    rng = np.random.default_rng(1)
+    for _ in range(100):
+        P = rng.standard_normal(X.shape) * 10 ** rng.uniform(-4, -1)
+        assert O.pga_objective(Xc + P, mask, obs, tau, Ms) >= Fc - 1e-9
+
+
 def test_pga_tolerance_stop_and_recovery():
     X, mask, obs, Ms = small_completion(I1=12, I2=10, rank=1, rho=0.7)
     Xk, info = O.pga(mask, obs, 0.01, 1.0, 500, Ms, tol=1e-6)
