@@ -614,6 +614,102 @@ def run_transform5(args):
                       "hbm_peak_gbs": peaks.get("hbm_gbs")}))
 
 
+def run_pga5(args):
+    """--case pga5: the large completion 540x960x3x120 (rank 15, noise 1e-3, 20%
+    observed, L_3 = DCT 3, L_4 = Q1 diag(d) Q2^T with cond 10, tau 0.5, step 1), a few
+    PGA iterations from a cold start on each path: FP64, FP32 and LT_MIXED (mode 120 on
+    the tensor cores).  Reports ms per iteration, the Jacobi share, and the relative
+    difference of the FP32 / mixed iterates from the FP64 one after the same iterations."""
+    import torch
+    from paper_2202_02870_gb300 import lt, synth
+    c = synth.config5()
+    dev = torch.device("cuda", 0)
+    shape = (540, 960, 3, 120)
+    tshape = tuple(reversed(shape))
+    mats = [lt.lt_make_dct(3), np.asarray(c["transforms"][1][1])]
+    ctx64 = lt.Context([3, 120], mats, lt.LT_FP64)
+    to_dev = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a.ravel(order="F"))).to(dt).reshape(
+        tuple(reversed(a.shape))).to(dev)
+    U = to_dev(c["U"], torch.float64)
+    Vt = to_dev(np.asfortranarray(np.swapaxes(c["V"], 0, 1)), torch.float64)
+    Xt = torch.empty(tshape, dtype=torch.float64, device=dev)
+    lt.lt_product(ctx64, U, Vt, Xt)
+    mask = torch.from_numpy(np.ascontiguousarray(c["mask"].ravel(order="F"))).reshape(tshape).to(dev)
+    obs64 = mask.double() * (Xt + to_dev(c["noise"], torch.float64))
+    del U, Vt, Xt
+    out = {"case": "pga5", "shape": list(shape), "iters": args.iters5}
+    res = {}
+    for name, prec in (("fp64", lt.LT_FP64), ("fp32", lt.LT_FP32), ("mixed", lt.LT_MIXED)):
+        ctx = ctx64 if prec == lt.LT_FP64 else lt.Context([3, 120], mats, prec)
+        dt = torch.float64 if prec == lt.LT_FP64 else torch.float32
+        obs = obs64.to(dt)
+        X = torch.zeros(tshape, dtype=dt, device=dev)
+        wsb = torch.empty(lt.lt_workspace_size(ctx, lt.LT_OP_PGA, 540, 960), dtype=torch.uint8,
+                          device=dev)
+        lt.lt_ctx_get_stats(ctx, reset=True)
+        lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        lt.lt_pga_complete(ctx, mask, obs, 0.5, 1.0, args.iters5, X, ws=wsb)
+        e1.record()
+        torch.cuda.synchronize()
+        st = lt.lt_ctx_get_stats(ctx, reset=True)
+        ms = e0.elapsed_time(e1) / args.iters5
+        res[name] = X.double()
+        out[name] = {"ms_per_iter": round(ms, 2), "iters_per_s": round(1e3 / ms, 3),
+                     "jacobi_share": round(st["jacobi"]["ms"] / max(sum(st[f]["ms"] for f in
+                                           ("transform", "jacobi", "gemm", "aux")), 1e-9), 4),
+                     "transform_ms_per_iter": round(st["transform"]["ms"] / args.iters5, 2),
+                     "tc_launches": st["tc_launches"]}
+        del X, wsb, obs
+        torch.cuda.empty_cache()
+    for name in ("fp32", "mixed"):
+        out[name]["rel_diff_vs_fp64"] = float(torch.linalg.norm(res[name] - res["fp64"]) /
+                                              torch.linalg.norm(res["fp64"]))
+    print(json.dumps(out))
+
+
+def run_svt5(args):
+    """--case svt5: lt_svt (tau 0.5) of a 540x960x3xI4 tensor with the large
+    completion's slice shape (first-iterate kind: P_Omega(N(0,1)) with 20% observed;
+    L_3 = DCT 3, L_4 = Q1 diag(d) Q2^T, cond 10), I4 = --i4 (40 by default: 120 slices,
+    whose per-CTA working matrices, 1.17 MB each in FP32, exceed L2).  The slices do not
+    fit shared memory: the Jacobi kernel keeps them in per-CTA workspace regions."""
+    import torch
+    from paper_2202_02870_gb300 import lt, synth
+    prec = {"fp64": lt.LT_FP64, "fp32": lt.LT_FP32, "mixed": lt.LT_MIXED}[args.precision]
+    dt = torch.float64 if prec == lt.LT_FP64 else torch.float32
+    rng = synth.rng_for(5, 1)
+    M4 = synth.conditioned_matrix(rng, args.i4, 10.0, two_sided=True)
+    ctx = lt.Context([3, args.i4], [lt.lt_make_dct(3), M4], prec)
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(20220705)
+    shape = (args.i4, 3, 960, 540)
+    G = torch.randn(shape, generator=g, device=dev, dtype=torch.float32)
+    G = (G * (torch.rand(shape, generator=g, device=dev) < 0.2)).to(dt)
+    D = torch.empty_like(G)
+    wsb = torch.empty(lt.lt_workspace_size(ctx, lt.LT_OP_SVT, 540, 960), dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        lt.lt_svt(ctx, G, 0.5, D, ws=wsb)
+    torch.cuda.synchronize()
+    lt.lt_ctx_get_stats(ctx, reset=True)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 1)
+    for _ in range(args.steps):
+        lt.lt_svt(ctx, G, 0.5, D, ws=wsb)
+    st = lt.lt_ctx_get_stats(ctx, reset=True)
+    j = st["jacobi"]
+    jms = j["ms"] / max(j["launches"], 1)
+    print(json.dumps({"case": "svt5", "precision": args.precision, "slices": 3 * args.i4,
+                      "jacobi_ms_per_launch": round(jms, 3),
+                      "slices_per_s": round(3 * args.i4 / (jms / 1e3), 2),
+                      "jacobi_gflops_executed": round(j["flops"] / max(j["ms"], 1e-9) / 1e6, 1),
+                      "algorithmic_bytes_per_launch": j["bytes"] / max(j["launches"], 1),
+                      "phase_ms_per_slice": {k: round(v / (3 * args.i4 * args.steps) / 1.97e6, 3)
+                                             for k, v in st["jacobi_phase_cycles"].items()}}))
+
+
 def run_reference(args):
     """The FP64 oracle as it stands, on the host cores: each step is a bounded sample of
     the same workload (ORACLE_ITERS_PER_STEP PGA iterations)."""
@@ -660,8 +756,13 @@ def main():
                     help="PGA iterations per call of the 64-problem batch")
     ap.add_argument("--product-steps", type=int, default=5,
                     help="timed calls of the fifth-order product leg (0 skips it)")
+    ap.add_argument("--i4", type=int, default=40,
+                    help="mode-4 size of --case svt5 (slices = 3 * i4)")
+    ap.add_argument("--iters5", type=int, default=3,
+                    help="PGA iterations per path of --case pga5")
     ap.add_argument("--case", default="pga",
-                    choices=["pga", "svt", "product", "product5", "transform5"],
+                    choices=["pga", "svt", "product", "product5", "transform5", "pga5",
+                             "svt5"],
                     help="pga: the benchmark line; svt/product: single-operation runs "
                          "used for profiling")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
@@ -683,6 +784,12 @@ def main():
         return
     if args.case == "transform5":
         run_transform5(args)
+        return
+    if args.case == "pga5":
+        run_pga5(args)
+        return
+    if args.case == "svt5":
+        run_svt5(args)
         return
     if args.case != "pga":
         run_case(args)
