@@ -206,8 +206,10 @@ jacobi_svt_kernel(const JArgs a) {
         W[idx] = (r < m && c < n) ? A[r + I1 * c] : T(0);
       }
     } else {
+      // consecutive threads fill consecutive rows of a column of W (the reads of the
+      // slice are strided; it comes from L2 once)
       for (int idx = threadIdx.x; idx < n * m; idx += blockDim.x) {
-        const int c = idx % n, r = idx / n;
+        const int r = idx % m, c = idx / m;
         W[r + (size_t)ld * c] = A[c + I1 * r];
       }
       for (int idx = threadIdx.x; idx < ld * np; idx += blockDim.x) {
