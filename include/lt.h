@@ -324,6 +324,36 @@ LT_API lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const in
 LT_API lt_status lt_product_noalloc(lt_ctx ctx, int64_t I1, int64_t l, int64_t I2,
                                     const void* A, const void* B, void* C, void* stream);
 
+/* Autotuning.  The kernel forms that are options of a context -- the Jacobi SVT's lanes
+ * per column pair and register blocking (LT_OPT_JACOBI_GROUP / LT_OPT_JACOBI_BLOCK) and,
+ * for LT_MIXED, the tensor-core tile width (LT_OPT_TC_TILE_N) -- are timed on the
+ * caller's data with CUDA events (one warm-up and three timed calls each), and the
+ * fastest is set on the context for the calls that follow.  Synchronises `stream`.
+ * report: host, may be NULL. */
+typedef struct {
+  int32_t jacobi_group;     /* chosen values (0 = the planner's default) */
+  int32_t jacobi_block;
+  int32_t tc_tile_n;
+  int32_t candidates;       /* forms timed */
+  double best_ms;           /* mean time per call of the chosen form */
+  double default_ms;        /* mean time per call of the planner's default form */
+} lt_tune_report;
+
+/* Times lt_svt(ctx, I1, I2, A, tau, D, ...) over the SVT kernel forms the slice shape
+ * admits (planner default; 8, 16, 32 lanes per pair; register blocks of 2 or 4
+ * columns for FP32).  D (not aliasing A) receives the result of the last call.
+ * Workspace as lt_svt; forms that would need more workspace are skipped. */
+LT_API lt_status lt_autotune_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau,
+                                 void* D, void* ws, size_t ws_bytes, void* stream,
+                                 lt_tune_report* report);
+
+/* Times lt_product(ctx, I1, l, I2, A, B, C, ...) over the tensor-core tile widths 32,
+ * 64, 128 and the default (LT_MIXED contexts; other precisions have one form and
+ * report it).  C receives the result of the last call.  Workspace as lt_product. */
+LT_API lt_status lt_autotune_product(lt_ctx ctx, int64_t I1, int64_t l, int64_t I2, const void* A,
+                                     const void* B, void* C, void* ws, size_t ws_bytes,
+                                     void* stream, lt_tune_report* report);
+
 /* Counters of the context since creation or the last reset (reset != 0 clears them
  * after reading).  Synchronises the device when LT_OPT_PROFILE is on or when Jacobi
  * flops are pending.  out: host. */

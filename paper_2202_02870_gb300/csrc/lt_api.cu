@@ -940,6 +940,94 @@ lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const int64_t* 
   return cuda_status(e);
 }
 
+}  // extern "C"
+
+namespace {
+
+// Mean CUDA-event time of `run` (one warm-up, three timed calls); +inf when a call
+// fails to enqueue.
+template <typename F>
+double time_calls(cudaStream_t st, F run) {
+  if (run() != LT_OK) return INFINITY;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return INFINITY;
+  cudaEventRecord(a, st);
+  lt_status s = LT_OK;
+  for (int i = 0; i < 3 && s == LT_OK; ++i) s = run();
+  cudaEventRecord(b, st);
+  float ms = 0.f;
+  const bool ok = cudaEventSynchronize(b) == cudaSuccess && cudaEventElapsedTime(&ms, a, b) == cudaSuccess;
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return (ok && s == LT_OK) ? ms / 3.0 : INFINITY;
+}
+
+}  // namespace
+
+extern "C" {
+
+lt_status lt_autotune_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau,
+                          void* D, void* ws, size_t ws_bytes, void* stream,
+                          lt_tune_report* report) {
+  if (check_ctx(ctx) != LT_OK || !A || !D || D == A) return LT_ERR_ARG;
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int keep_g = c.jacobi_group, keep_b = c.jacobi_pairwise;
+  struct Form { int g, b; };
+  std::vector<Form> forms = {{0, 0}, {8, 1}, {16, 1}, {32, 1}};
+  if (c.elem == 4) forms.insert(forms.end(), {{8, 2}, {16, 2}, {32, 2}});
+  double best = INFINITY, dflt = INFINITY;
+  Form pick = {keep_g, keep_b};
+  int timed = 0;
+  for (const Form& f : forms) {
+    c.jacobi_group = f.g;
+    c.jacobi_pairwise = f.b;
+    size_t need = 0;
+    if (lt_workspace_size(ctx, LT_OP_SVT, I1, I2, 0, &need) != LT_OK || need > ws_bytes) continue;
+    const double ms = time_calls(st, [&] { return lt_svt(ctx, I1, I2, A, tau, D, ws, ws_bytes, stream); });
+    if (!std::isfinite(ms)) continue;
+    ++timed;
+    if (f.g == 0 && f.b == 0) dflt = ms;
+    if (ms < best) { best = ms; pick = f; }
+  }
+  if (timed == 0) {
+    c.jacobi_group = keep_g;
+    c.jacobi_pairwise = keep_b;
+    return cuda_status(cudaGetLastError()) == LT_OK ? LT_ERR_ARG : LT_ERR_CUDA;
+  }
+  c.jacobi_group = pick.g;
+  c.jacobi_pairwise = pick.b;
+  if (report) *report = lt_tune_report{pick.g, pick.b, c.tc_tile_n, timed, best, dflt};
+  return LT_OK;
+}
+
+lt_status lt_autotune_product(lt_ctx ctx, int64_t I1, int64_t l, int64_t I2, const void* A,
+                              const void* B, void* C, void* ws, size_t ws_bytes, void* stream,
+                              lt_tune_report* report) {
+  if (check_ctx(ctx) != LT_OK || !A || !B || !C) return LT_ERR_ARG;
+  Ctx& c = *reinterpret_cast<Ctx*>(ctx);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int keep = c.tc_tile_n;
+  std::vector<int> forms = {0};
+  if (c.prec == LT_MIXED) forms.insert(forms.end(), {32, 64, 128});
+  double best = INFINITY, dflt = INFINITY;
+  int pick = keep, timed = 0;
+  for (int tn : forms) {
+    c.tc_tile_n = tn;
+    const double ms = time_calls(st, [&] {
+      return lt_product(ctx, I1, l, I2, A, B, C, ws, ws_bytes, stream);
+    });
+    if (!std::isfinite(ms)) continue;
+    ++timed;
+    if (tn == 0) dflt = ms;
+    if (ms < best) { best = ms; pick = tn; }
+  }
+  c.tc_tile_n = timed ? pick : keep;
+  if (timed == 0) return LT_ERR_ARG;
+  if (report) *report = lt_tune_report{c.jacobi_group, c.jacobi_pairwise, pick, timed, best, dflt};
+  return LT_OK;
+}
+
 lt_status lt_ctx_get_stats(lt_ctx ctx, lt_stats* out, int reset) {
   if (!ctx || !out) return LT_ERR_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);

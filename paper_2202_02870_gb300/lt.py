@@ -51,6 +51,12 @@ class lt_kernel_stats(C.Structure):
                 ("bytes", C.c_double)]
 
 
+class lt_tune_report(C.Structure):
+    _fields_ = [("jacobi_group", C.c_int32), ("jacobi_block", C.c_int32),
+                ("tc_tile_n", C.c_int32), ("candidates", C.c_int32),
+                ("best_ms", C.c_double), ("default_ms", C.c_double)]
+
+
 class lt_stats(C.Structure):
     _fields_ = [("k", lt_kernel_stats * 4), ("jacobi_phase_cycles", C.c_double * 10),
                 ("tc_launches", C.c_int64)]
@@ -81,6 +87,10 @@ SIGNATURES = {
                                           C.POINTER(lt_pga_report), _vp, _sz, _vp]),
     "lt_product_noalloc": (C.c_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp]),
     "lt_truncate": (C.c_int, [_vp, _i64, _i64, _vp, _i64, _vp, _vp, _sz, _vp]),
+    "lt_autotune_svt": (C.c_int, [_vp, _i64, _i64, _vp, _dbl, _vp, _vp, _sz, _vp,
+                                  C.POINTER(lt_tune_report)]),
+    "lt_autotune_product": (C.c_int, [_vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _sz, _vp,
+                                      C.POINTER(lt_tune_report)]),
     "lt_norms": (C.c_int, [_vp, _i64, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
     "lt_ctx_get_stats": (C.c_int, [_vp, C.POINTER(lt_stats), C.c_int]),
     "lt_last_device_status": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
@@ -356,6 +366,33 @@ def lt_pga_complete_batched(ctxs, masks, obss, taus, steps, iters, Xs, reports=N
     if reports is not None:
         reports.append(rep_arr)
     return Xs
+
+
+def lt_autotune_svt(ctx, A, tau, D, ws=None, stream=None) -> lt_tune_report:
+    """Times the SVT kernel forms on A and sets the fastest on the context."""
+    _require(A, ctx, "A"); _require(D, ctx, "D")
+    I1, I2 = _dims(A)
+    need = lt_workspace_size(ctx, LT_OP_SVT, I1, I2)
+    ws, nb = _workspace(ctx, need, A.device, ws)
+    rep = lt_tune_report()
+    _check("lt_autotune_svt", lib().lt_autotune_svt(ctx.handle, I1, I2, _ptr(A), float(tau), _ptr(D),
+                                                    _ptr(ws), nb, _stream(stream), C.byref(rep)))
+    return rep
+
+
+def lt_autotune_product(ctx, A, B, Cout, ws=None, stream=None) -> lt_tune_report:
+    """Times the tensor-core tile widths of lt_product on A, B and sets the fastest."""
+    for t, n in ((A, "A"), (B, "B"), (Cout, "C")):
+        _require(t, ctx, n)
+    I1, l = _dims(A)
+    _, I2 = _dims(B)
+    need = lt_workspace_size(ctx, LT_OP_PRODUCT, I1, l, I2)
+    ws, nb = _workspace(ctx, need, A.device, ws)
+    rep = lt_tune_report()
+    _check("lt_autotune_product", lib().lt_autotune_product(
+        ctx.handle, I1, l, I2, _ptr(A), _ptr(B), _ptr(Cout), _ptr(ws), nb, _stream(stream),
+        C.byref(rep)))
+    return rep
 
 
 def lt_ctx_get_stats(ctx, reset: bool = False) -> dict:

@@ -107,3 +107,43 @@ def test_truncate_rejects_negative_rank():
     A = torch.zeros((3, 5, 6), dtype=torch.float64, device="cuda")
     with pytest.raises(lt.LtError):
         lt.lt_truncate(ctx, A, -1, A)
+
+
+@pytest.mark.parametrize("prec", [lt.LT_FP64, lt.LT_FP32])
+def test_autotune_svt_picks_a_form_and_keeps_parity(prec):
+    """lt_autotune_svt times the SVT kernel forms on the caller's slices, sets the fastest
+    on the context (never slower than the planner's default by its own measurement), and
+    the SVT computed with it still matches the oracle."""
+    rng = np.random.default_rng(31)
+    full = (48, 56, 3, 2)
+    A = rng.standard_normal(full)
+    tr = [("dct", 3), ("dct", 2)]
+    ctx = make_ctx(tr, prec)
+    dt = dtype_of(prec)
+    Ad, D = to_dev(A, dt), empty_dev(full, dt)
+    rep = lt.lt_autotune_svt(ctx, Ad, 0.5, D)
+    assert rep.candidates >= 4 and rep.best_ms <= rep.default_ms
+    D2 = empty_dev(full, dt)
+    lt.lt_svt(ctx, Ad, 0.5, D2)
+    torch.cuda.synchronize()
+    ref = O.svt(A, 0.5, oracle_mats(tr))
+    assert rel(from_dev(D2, full), ref) <= TOL[prec]
+    assert lt.lt_last_device_status(ctx) == 0
+    with pytest.raises(lt.LtError):  # D must not alias A
+        lt.lt_autotune_svt(ctx, Ad, 0.5, Ad)
+
+
+def test_autotune_product_picks_a_tile_width():
+    rng = np.random.default_rng(32)
+    A = rng.uniform(-1, 1, (128, 64, 4))
+    B = rng.uniform(-1, 1, (64, 96, 4))
+    tr = [("dct", 4)]
+    ctx = make_ctx(tr, lt.LT_MIXED)
+    Cd = empty_dev((128, 96, 4), torch.float32)
+    Ad, Bd = to_dev(A, torch.float32), to_dev(B, torch.float32)
+    rep = lt.lt_autotune_product(ctx, Ad, Bd, Cd)
+    assert rep.candidates == 4 and rep.tc_tile_n in (0, 32, 64, 128)
+    assert rep.best_ms <= rep.default_ms
+    lt.lt_product(ctx, Ad, Bd, Cd)
+    torch.cuda.synchronize()
+    assert rel(from_dev(Cd, (128, 96, 4)), O.product(A, B, oracle_mats(tr))) <= 1e-5
