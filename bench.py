@@ -103,6 +103,24 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, ws, device):
+    """The largest value of x over the ranks of the process group (x itself at N = 1):
+    the job's step time is the slowest rank's."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, ws, step_ms):
+    """Whole-job throughput: the units every rank processed in a step over the slowest
+    rank's step time (ms)."""
+    return ws * units_per_rank / (step_ms / 1e3)
+
+
 def problem_inputs(rank):
     """Seeded config-2 problem; rank r uses problem index r."""
     from paper_2202_02870_gb300 import synth
@@ -265,12 +283,8 @@ def run_ours(args):
         X64, ms64, wall64, st64, rep64 = run_path(ctx64, obs64, torch.float64, args.steps,
                                                   args.warmup, True)
     clocks = clk.summary()
-    step_ms = statistics.mean(ms64)
-    if ws > 1:
-        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = ws * iters / (step_ms / 1e3)
+    step_ms = max_over_ranks(statistics.mean(ms64), ws, dev)
+    value = job_rate(iters, ws, step_ms)
 
     jac = st64["jacobi"]
     tra = st64["transform"]
@@ -343,11 +357,7 @@ def run_ours(args):
         e2e_ms.append(e0.elapsed_time(e1))
     lt.lt_ctx_set_option(ctx64, lt.LT_OPT_PROFILE, 0)
     lt.lt_ctx_get_stats(ctx64, reset=True)
-    e2e_step = statistics.mean(e2e_ms)
-    if ws > 1:
-        t = torch.tensor([e2e_step], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(statistics.mean(e2e_ms), ws, dev)
 
     # ---------------- CPU baseline: the oracle on the host cores (rank 0, N = 1 only)
     cpu = None
@@ -402,7 +412,7 @@ def run_ours(args):
                 "unit": "GFLOP/s", "peak": FP64_PEAK_GFLOPS,
                 "hbm_gbs": round(tra["bytes"] / max(tra["ms"], 1e-9) / 1e6, 1),
                 "hbm_peak_gbs": peaks.get("hbm_gbs")},
-            "e2e": {"value": round(ws * iters / (e2e_step / 1e3), 5), "unit": "iters/s",
+            "e2e": {"value": round(job_rate(iters, ws, e2e_step), 5), "unit": "iters/s",
                     "ms_per_step": round(e2e_step, 3),
                     "h2d_bytes_per_step": int(N + N * 8), "d2h_bytes_per_step": int(N * 8)},
             "gpu_launches": int(gpu_launches),
