@@ -19,8 +19,9 @@ from tests.gpu_util import dtype_of, empty_dev, from_dev, make_ctx, oracle_mats,
 
 pytestmark = pytest.mark.gpu
 
-U = {lt.LT_FP64: 2.0 ** -53, lt.LT_FP32: 2.0 ** -24}
-FLOOR = {lt.LT_FP64: 1e-12, lt.LT_FP32: 1e-5}
+# unit roundoff of the arithmetic: LT_MIXED's face-wise GEMM carries about 21 bits
+U = {lt.LT_FP64: 2.0 ** -53, lt.LT_FP32: 2.0 ** -24, lt.LT_MIXED: 2.0 ** -21}
+FLOOR = {lt.LT_FP64: 1e-12, lt.LT_FP32: 1e-5, lt.LT_MIXED: 1e-5}
 
 
 def tol_for(prec, Ms):
@@ -48,7 +49,7 @@ def kron_rows(Ms):
     return K
 
 
-@pytest.mark.parametrize("prec", [lt.LT_FP64, lt.LT_FP32])
+@pytest.mark.parametrize("prec", [lt.LT_FP64, lt.LT_FP32, lt.LT_MIXED])
 def test_config3_product_sampled_tubes(config3, prec):
     A, B = config3["A"], config3["B"]
     Ms = oracle_mats(config3["transforms"])
@@ -71,6 +72,8 @@ def test_config3_product_sampled_tubes(config3, prec):
         got = Cd[:, :, :, j, i].double().cpu().numpy().transpose(2, 1, 0)
         errs.append(rel(got, ref))
     assert max(errs) <= tol, (max(errs), tol, kappa)
+    if prec == lt.LT_MIXED:  # the face-wise GEMM ran on the tensor cores
+        assert lt.lt_ctx_get_stats(ctx)["tc_launches"] == 1
 
 
 def test_config3_svt_sampled_slices(config3):

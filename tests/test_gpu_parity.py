@@ -500,16 +500,40 @@ def test_pga_batched_vs_oracle(prec):
         assert rel(from_dev(Xb, p["obs"].shape), ref) <= TOL[prec]
 
 
-def test_pga_batched_config4_full():
+def test_pga_batched_with_tensor_core_passes_equals_single_runs():
+    """LT_MIXED batch with the mode-4 products routed to the tensor cores
+    (LT_OPT_TC_MODE_MIN = 8): the tcgen05 kernels captured in the batch graph give the
+    same iterates as separate calls, bit for bit, and stay within the bound of the
+    oracle."""
+    probs = batch_problems(SMALL_BATCH, lt.LT_MIXED)
+    for p in probs:
+        lt.lt_ctx_set_option(p["ctx"], lt.LT_OPT_TC_MODE_MIN, 8)
+    Xs, reps = run_batched(probs, lt.LT_MIXED, 7)
+    assert sum(lt.lt_ctx_get_stats(p["ctx"])["tc_launches"] for p in probs) > 0
+    for p, Xb, rep in zip(probs, Xs, reps):
+        Xs1 = to_dev(np.zeros(p["obs"].shape), torch.float32)
+        lt.lt_pga_complete(p["ctx"], to_dev(p["mask"]), to_dev(p["obs"], torch.float32), p["tau"],
+                           1.0, 7, Xs1)
+        torch.cuda.synchronize()
+        assert torch.equal(Xb, Xs1)
+        assert rep.iters_done == 7 and rep.device_status == 0
+        ref, _ = O.pga(p["mask"], p["obs"], p["tau"], 1.0, 7, p["Ms"])
+        assert rel(from_dev(Xb, p["obs"].shape), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [lt.LT_FP32, lt.LT_MIXED])
+def test_pga_batched_config4_full(prec):
     """The 64-problem batch of uneven sizes (I1 x I2 from 64 x 48 to 512 x 384, I3 = 3,
-    I4 in {8, 16, 32, 64}), FP32: every problem completes its iterations without device
-    errors, and two of them equal their single-problem runs bit for bit."""
+    I4 in {8, 16, 32, 64}), FP32 and LT_MIXED (the benchmark's batched leg; its I4 = 64
+    problems put the mode-4 products on the tensor cores): every problem completes its
+    iterations without device errors, and two of them (for LT_MIXED one with I4 = 64)
+    equal their single-problem runs bit for bit."""
     shapes = synth.config4_shapes()
     rng = np.random.default_rng(4)
     ctxs, masks, obss, Xs = [], [], [], []
     for i, sh in enumerate(shapes):
         full = (sh["I1"], sh["I2"]) + sh["trailing"]
-        ctxs.append(make_ctx([("dct", n) for n in sh["trailing"]], lt.LT_FP32))
+        ctxs.append(make_ctx([("dct", n) for n in sh["trailing"]], prec))
         m = (rng.random(full) < sh["rho"]).astype(np.uint8)
         masks.append(to_dev(m))
         obss.append(to_dev(m * rng.standard_normal(full), torch.float32))
@@ -518,7 +542,11 @@ def test_pga_batched_config4_full():
     lt.lt_pga_complete_batched(ctxs, masks, obss, [0.5] * 64, [1.0] * 64, 4, Xs, reports=reps)
     torch.cuda.synchronize()
     assert all(r.iters_done == 4 and r.device_status == 0 for r in reps[0])
-    for i in (0, 37):
+    check = [0, 37]
+    if prec == lt.LT_MIXED:
+        check[1] = next(i for i, sh in enumerate(shapes) if sh["trailing"][1] == 64)
+        assert lt.lt_ctx_get_stats(ctxs[check[1]])["tc_launches"] > 0
+    for i in check:
         X1 = torch.zeros_like(Xs[i])
         lt.lt_pga_complete(ctxs[i], masks[i], obss[i], 0.5, 1.0, 4, X1)
         torch.cuda.synchronize()
