@@ -31,6 +31,10 @@ Readings of the paper taken here (the paper is ambiguous or garbled at these poi
   gradient step l_f^{-1} = step, l_f = 1 in the paper); the threshold is applied
   unscaled in the transform domain as Algorithm 4 does; the stopping quantity is
   ||Y^k - X^{k+1}||_F / ||X^{k+1}||_F (Sec. 5), taken as ||Y^k||_F when X^{k+1} = 0.
+* Fourier operator (Sec. 2, t-product; Sec. 5, fft along mode 3): M_3 = F_{I3}
+  unnormalised and complex, M_4, ..., M_K real; the SVT thresholds the complex slices
+  of L(A) at tau as Algorithm 4 does, and L^{-1} keeps the real part.  The norm relation
+  printed after the definition of L reads M_i M_i^* = alpha_i I (F: alpha = n).
 """
 from __future__ import annotations
 
@@ -41,7 +45,8 @@ import numpy as np
 __all__ = [
     "dct_matrix", "cproduct_matrix", "mode_product", "transform", "inverse_transform",
     "slices", "from_slices", "facewise", "product", "identity", "transpose",
-    "svd", "svt", "truncate", "ranks_and_norms", "nuclear_norm", "pga", "pga_objective",
+    "svd", "svt", "truncate", "ranks_and_norms", "nuclear_norm", "fourier_matrix",
+    "fourier_transform", "fourier_inverse", "tproduct", "tsvt", "pga", "pga_objective",
     "psnr", "rse",
 ]
 
@@ -241,6 +246,55 @@ def nuclear_norm(A: np.ndarray, Ms) -> float:
 
 
 # ----------------------------------------------------------------------------------
+# The Fourier operator (t-product): M_3 = F_{I3} of Sec. 2, complex
+# ----------------------------------------------------------------------------------
+def fourier_matrix(n: int) -> np.ndarray:
+    """F_n of Sec. 2: (F_n)_{i,j} = omega^{(i-1)(j-1)}, omega = exp(-2 pi i / n)
+    (unnormalised; F_n F_n^* = n I)."""
+    k = np.arange(n)
+    return np.exp(-2j * np.pi * np.outer(k, k) / n)
+
+
+def fourier_transform(X: np.ndarray, Ms_rest=()) -> np.ndarray:
+    """L(X) with M_3 = F_{I3} (the t-product's transform, Sec. 2) and real M_4..M_K:
+    X x_3 F x_4 M_4 ... x_K M_K, complex."""
+    Y = mode_product(np.asarray(X, dtype=np.complex128), fourier_matrix(X.shape[2]), 3)
+    for k, M in enumerate(Ms_rest, start=4):
+        Y = mode_product(Y, np.asarray(M, dtype=np.float64), k)
+    return Y
+
+
+def fourier_inverse(Yh: np.ndarray, Ms_rest=()) -> np.ndarray:
+    """L^{-1} of `fourier_transform`; the real part of the result (the imaginary part
+    of the inverse of a conjugate-symmetric transform-domain tensor is rounding)."""
+    K = len(Ms_rest) + 3
+    for k in range(K, 3, -1):
+        Yh = mode_product(Yh, np.linalg.inv(np.asarray(Ms_rest[k - 4], dtype=np.float64)), k)
+    n = Yh.shape[2]
+    return np.real(mode_product(Yh, np.linalg.inv(fourier_matrix(n)), 3))
+
+
+def tproduct(A: np.ndarray, B: np.ndarray, Ms_rest=()) -> np.ndarray:
+    """*_L-product with M_3 = F (the t-product of Kilmer and Martin for third order),
+    Algorithm 2 on complex transform-domain slices."""
+    Ah = slices(fourier_transform(A, Ms_rest))
+    Bh = slices(fourier_transform(B, Ms_rest))
+    Ch = np.stack([Ah[:, :, p] @ Bh[:, :, p] for p in range(Ah.shape[2])], axis=2)
+    return fourier_inverse(from_slices(Ch, A.shape[2:]), Ms_rest)
+
+
+def tsvt(A: np.ndarray, tau: float, Ms_rest=()) -> np.ndarray:
+    """*_L-SVT with M_3 = F, Algorithm 4: per complex transform-domain slice
+    U max(S - tau, 0) V^H, threshold applied unscaled to the slices of L(A)."""
+    Ah = slices(fourier_transform(A, Ms_rest))
+    Dh = np.empty_like(Ah)
+    for p in range(Ah.shape[2]):
+        u, s, vh = np.linalg.svd(Ah[:, :, p], full_matrices=False)
+        Dh[:, :, p] = (u * np.maximum(s - tau, 0.0)) @ vh
+    return fourier_inverse(from_slices(Dh, A.shape[2:]), Ms_rest)
+
+
+# ----------------------------------------------------------------------------------
 # Completion by PGA (Sec. 4: Eqs. 50-53, Algorithm 5)
 # ----------------------------------------------------------------------------------
 def pga_objective(X, mask, obs, tau, Ms) -> float:
@@ -251,11 +305,13 @@ def pga_objective(X, mask, obs, tau, Ms) -> float:
 
 
 def pga(mask, obs, tau, step, iters, Ms, tol=0.0, X0=None, momentum=True,
-        objective=False, mu0=0.0, nu=0.9):
+        objective=False, mu0=0.0, nu=0.9, fourier=False):
     """Tensor completion by PGA, Algorithm 5.  With mu0 = 0 (default) the threshold is
     the fixed mu = tau; with mu0 > 0 it follows the continuation of Algorithm 5,
     mu_{k+1} = max(nu mu_k, mu_bar), read with mu_bar = tau: iteration k (0-based)
-    thresholds at step * max(nu^k mu0, tau).
+    thresholds at step * max(nu^k mu0, tau).  fourier=True uses M_3 = F (TNN-PGA-F of
+    Sec. 5): the SVT is `tsvt` with Ms = [M_4, ..., M_K] (the objective is then not
+    available).
 
         X^0 = X^1 = X0 (zeros by default), t_0 = t_1 = 1
         repeat:  Y^k = X^k + ((t_{k-1} - 1) / t_k) (X^k - X^{k-1})      (Eq. 52)
@@ -270,6 +326,8 @@ def pga(mask, obs, tau, step, iters, Ms, tol=0.0, X0=None, momentum=True,
     Returns (X_final, info) with info = {"iters", "residual" (list), "objective" (list
     or None), "t" (final t_k)}.
     """
+    if fourier and objective:
+        raise ValueError("the objective is defined for real transforms only")
     m = np.asarray(mask).astype(np.float64)
     obs = np.asarray(obs, dtype=np.float64)
     X = np.zeros_like(obs) if X0 is None else np.array(X0, dtype=np.float64)
@@ -282,7 +340,7 @@ def pga(mask, obs, tau, step, iters, Ms, tol=0.0, X0=None, momentum=True,
         Y = X + beta * (X - X_prev)
         G = Y - step * m * (Y - obs)
         mu = max(nu ** k_done * mu0, tau) if mu0 > 0 else tau
-        X_new = svt(G, step * mu, Ms)
+        X_new = tsvt(G, step * mu, Ms) if fourier else svt(G, step * mu, Ms)
         nx = float(np.linalg.norm(X_new))
         ny = float(np.linalg.norm(Y - X_new))
         r = ny / nx if nx > 0 else float(np.linalg.norm(Y))

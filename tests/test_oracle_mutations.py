@@ -109,6 +109,20 @@ def _ranks_slice_relative(A, Ms, unit_roundoff=2.0 ** -53):
     out["multirank"] = np.array(rho)
     return out
 
+_ORIG_TSVT = O.tsvt
+
+
+def _fourier_one_based(n):
+    # omega^{ij} with 1-based i, j instead of omega^{(i-1)(j-1)}
+    k = np.arange(1, n + 1)
+    return np.exp(-2j * np.pi * np.outer(k, k) / n)
+
+
+def _tsvt_unitary_threshold(A, tau, Ms_rest=()):
+    # threshold the slices of F/sqrt(n)-transformed data instead of F-transformed data
+    return _ORIG_TSVT(A, tau * math.sqrt(A.shape[2]), Ms_rest)
+
+
 MUTATIONS = [
     ("dct_matrix", _dct_delta_ij, [pins.test_dct_matrix_closed_forms_and_scipy]),
     ("cproduct_matrix", _cprod_no_Z, [pins.test_cproduct_matrix_closed_forms]),
@@ -124,6 +138,10 @@ MUTATIONS = [
     ("pga", _pga_continuation_late, [pins.test_pga_continuation_schedule_and_limit]),
     ("truncate", _truncate_off_by_one, [pins.test_truncate_is_the_eckart_young_product]),
     ("ranks_and_norms", _ranks_slice_relative, [pins.test_ranks_and_norms_on_prescribed_ranks]),
+    ("fourier_matrix", _fourier_one_based,
+     [pins.test_fourier_matrix_is_numpy_fft_and_scaled_unitary]),
+    ("tsvt", _tsvt_unitary_threshold,
+     [lambda: pins.test_tsvt_is_the_prox_of_the_fourier_nuclear_norm((4,))]),
 ]
 
 

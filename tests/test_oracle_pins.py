@@ -435,3 +435,132 @@ def test_pga_tolerance_stop_and_recovery():
     Xk, info = O.pga(mask, obs, 0.01, 1.0, 500, Ms, tol=1e-6)
     assert info["iters"] < 500 and info["residual"][-1] <= 1e-6
     assert O.rse(X, Xk) < 0.05
+
+
+# ---------------------------------------------------------------- Fourier (t-product)
+def bcirc_product(A, B):
+    """The t-product from its circulant definition (Kilmer and Martin), no transform:
+    C = fold(bcirc(A) unfold(B)), i.e. C_k = sum_j A_{(k - j) mod n} B_j on the frontal
+    slices."""
+    n = A.shape[2]
+    C = np.zeros((A.shape[0], B.shape[1], n))
+    for k in range(n):
+        for j in range(n):
+            C[:, :, k] += A[:, :, (k - j) % n] @ B[:, :, j]
+    return C
+
+
+def tnn_fourier(Y, Ms_rest=()):
+    """sum over the transform-domain slices of L(Y) = fft along mode 3 (numpy's FFT),
+    then the real M_4, ..., of their nuclear norms (numpy's SVD)."""
+    Yh = np.fft.fft(Y, axis=2)
+    for k, M in enumerate(Ms_rest, start=3):
+        Yh = np.moveaxis(np.tensordot(M, Yh, axes=(1, k)), 0, k)
+    S = Yh.reshape(Y.shape[0], Y.shape[1], -1, order="F")
+    return float(sum(np.linalg.svd(S[:, :, p], compute_uv=False).sum()
+                     for p in range(S.shape[2])))
+
+
+def test_fourier_matrix_is_numpy_fft_and_scaled_unitary():
+    for n in (1, 2, 3, 4, 7):
+        F = O.fourier_matrix(n)
+        assert np.allclose(F, np.fft.fft(np.eye(n), axis=0), atol=1e-13)
+        assert np.allclose(F @ F.conj().T, n * np.eye(n), atol=1e-12)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5])
+def test_tproduct_is_the_block_circulant_product(n):
+    """Third order: A *_L B with M_3 = F (Sec. 2) is the t-product fold(bcirc(A)
+    unfold(B)); n = 1 is the matrix product."""
+    rng = np.random.default_rng(40 + n)
+    A, B = rand(rng, 4, 3, n), rand(rng, 3, 5, n)
+    C = O.tproduct(A, B)
+    assert rel(C, bcirc_product(A, B)) < 1e-13
+    if n == 1:
+        assert rel(C[:, :, 0], A[:, :, 0] @ B[:, :, 0]) < 1e-14
+
+
+def test_tproduct_fourth_order_splits_along_mode_4():
+    """With a real invertible M_4 the product is, for each mode-4 index of the
+    M_4-transformed operands, the third-order t-product, then M_4^{-1} (the mode
+    products on different modes commute)."""
+    rng = np.random.default_rng(44)
+    M4 = rand_invertible(rng, 3)
+    A, B = rand(rng, 4, 3, 5, 3), rand(rng, 3, 2, 5, 3)
+    At, Bt = O.mode_product(A, M4, 4), O.mode_product(B, M4, 4)
+    Ct = np.stack([bcirc_product(At[..., j], Bt[..., j]) for j in range(3)], axis=3)
+    assert rel(O.tproduct(A, B, [M4]), O.mode_product(Ct, np.linalg.inv(M4), 4)) < 1e-12
+
+
+def test_tsvt_special_cases():
+    """n = 1: the matrix SVT.  Equal frontal slices A_0: F(A) has the one nonzero slice
+    n A_0, whose SVT at tau is n D_{tau/n}(A_0), so every frontal slice of the result is
+    D_{tau/n}(A_0).  tau = 0 returns A; tau above every singular value returns 0."""
+    rng = np.random.default_rng(45)
+    A0 = rand(rng, 6, 4)
+
+    def msvt(M, t):
+        u, s, vt = np.linalg.svd(M, full_matrices=False)
+        return (u * np.maximum(s - t, 0)) @ vt
+
+    assert rel(O.tsvt(A0[:, :, None], 0.7)[:, :, 0], msvt(A0, 0.7)) < 1e-13
+    n = 5
+    A = np.repeat(A0[:, :, None], n, axis=2)
+    D = O.tsvt(A, 2.0)
+    for k in range(n):
+        assert rel(D[:, :, k], msvt(A0, 2.0 / n)) < 1e-12
+    X = rand(rng, 5, 4, 3, 2)
+    Ms = [O.dct_matrix(2)]
+    assert rel(O.tsvt(X, 0.0, Ms), X) < 1e-13
+    assert np.abs(O.tsvt(X, 1e6, Ms)).max() == 0.0
+
+
+@pytest.mark.parametrize("trailing", [(4,), (3, 2)])
+def test_tsvt_is_the_prox_of_the_fourier_nuclear_norm(trailing):
+    """With M_3 = F (M_3 M_3^* = n I) and orthonormal M_4, ||Y||_F^2 = ||L(Y)||_F^2 / n,
+    so thresholding the slices of L(A) at tau minimises (tau / n) sum_p ||L(Y)^p||_* +
+    1/2 ||Y - A||_F^2 over real Y (the unconstrained minimiser is conjugate-symmetric
+    along mode 3, hence real).  Checked against random real perturbations, with the
+    nuclear norm taken from numpy's FFT and SVD."""
+    rng = np.random.default_rng(46)
+    Ms = [O.dct_matrix(n) for n in trailing[1:]]
+    A = rand(rng, 5, 4, *trailing)
+    tau, n = 1.1, trailing[0]
+    Dt = O.tsvt(A, tau, Ms)
+
+    def F(Y):
+        return tau / n * tnn_fourier(Y, Ms) + 0.5 * np.linalg.norm(Y - A) ** 2
+
+    f0 = F(Dt)
+    assert f0 < F(A) and f0 < F(np.zeros_like(A))
+    for _ in range(150):
+        P = rand(rng, *A.shape) * 10 ** rng.uniform(-4, 0)
+        assert F(Dt + P) >= f0 - 1e-12
+
+
+def test_pga_fourier_full_observation_and_limit():
+    """TNN-PGA-F: Omega = everything with step 1 gives tsvt(M) at every iterate; on a
+    partial mask the limit minimises 1/2 ||P(X - M)||^2 + (tau / n) sum_p ||F(X)^p||_*
+    (the step's threshold step tau is the prox of step (tau / n) TNN_F, by the pin
+    above)."""
+    rng = np.random.default_rng(47)
+    n = 3
+    U, V = rand(rng, 8, 2, n, 4), rand(rng, 7, 2, n, 4)
+    Ms = [O.dct_matrix(4)]
+    X = O.tproduct(U, np.transpose(V, (1, 0, 2, 3)), Ms)
+    Xk, _ = O.pga(np.ones(X.shape, np.uint8), X, 0.3, 1.0, 4, Ms, fourier=True)
+    assert rel(Xk, O.tsvt(X, 0.3, Ms)) < 1e-13
+    mask = (rng.random(X.shape) < 0.6).astype(np.uint8)
+    obs = mask * X
+    tau = 0.05
+    Xf, _ = O.pga(mask, obs, tau, 1.0, 500, Ms, fourier=True)
+
+    def F(Y):
+        return 0.5 * float(np.sum((mask * (Y - obs)) ** 2)) + tau / n * tnn_fourier(Y, Ms)
+
+    f0 = F(Xf)
+    for _ in range(100):
+        P = rand(rng, *X.shape) * 10 ** rng.uniform(-4, -1)
+        assert F(Xf + P) >= f0 - 1e-9
+    with pytest.raises(ValueError):
+        O.pga(mask, obs, tau, 1.0, 2, Ms, fourier=True, objective=True)
