@@ -322,6 +322,12 @@ def run_ours(args):
     fp32_leg = single_leg(lt.LT_FP32, "f32")
     mixed_leg = single_leg(lt.LT_MIXED, "f32 + split-tf32x3 tensor cores")
 
+    # ---------------- the Fourier operator (TNN-PGA-F, Sec. 5) on the same observations
+    fourier = None
+    if args.fourier_steps > 0:
+        fourier = fourier_leg(args, dev, ws, mask_d, obs64, c, flush,
+                              rank == 0 and ws == 1 and not args.no_cpu)
+
     # ---------------- batched: the 64 uneven problems of one batch, FP32
     batched = None
     if args.batched_steps > 0:
@@ -397,6 +403,7 @@ def run_ours(args):
             "fp32": fp32_leg,
             "autotune": tuned,
             "batched": batched,
+            "fourier": fourier,
             "product_256x256x16x16x8": product,
             "roofline": {"kernel": "jacobi_svt (FP64)", "bound": "alu",
                          "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
@@ -424,6 +431,74 @@ def run_ours(args):
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def fourier_leg(args, dev, ws, mask_d, obs64, c, flush, cpu):
+    """TNN-PGA-F: PGA with M_3 = F_3 (t-product operator) and M_4 = DCT 32 on the
+    144x176x3x32 observations (lt_ctx_create_fourier), FP64 and FP32; `--fourier-iters`
+    iterations per step, 3 warm-up steps, `--fourier-steps` timed steps with CUDA
+    events.  With `cpu` (rank 0, N = 1) the oracle's TNN-PGA-F is timed on a sample of
+    two iterations of the same problem."""
+    import torch
+    from paper_2202_02870_gb300 import lt
+    iters = args.fourier_iters
+    out = {"operator": "F_3 (t-product) x DCT 32", "iters_per_step": iters,
+           "slices": "32 real 144x176 + 32 realified 288x352 per iteration"}
+    X64 = None
+    for prec, label, dt in ((lt.LT_FP64, "f64", torch.float64), (lt.LT_FP32, "f32", torch.float32)):
+        ctx = lt.lt_ctx_create_fourier([3, 32], [lt.lt_make_dct(32)], prec)
+        obs = obs64.to(dt)
+        X = torch.zeros_like(obs)
+        wsb = torch.empty(lt.lt_workspace_size(ctx, lt.LT_OP_PGA, 144, 176), dtype=torch.uint8,
+                          device=dev)
+        rep = lt.lt_pga_report()
+        for _ in range(3):
+            X.zero_()
+            lt.lt_pga_complete(ctx, mask_d, obs, c["tau"], c["step"], iters, X, report=rep, ws=wsb)
+        torch.cuda.synchronize()
+        lt.lt_ctx_get_stats(ctx, reset=True)
+        lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 1)
+        st = torch.cuda.current_stream()
+        ms = []
+        for _ in range(args.fourier_steps):
+            flush.zero_()
+            X.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            lt.lt_pga_complete(ctx, mask_d, obs, c["tau"], c["step"], iters, X, report=rep, ws=wsb)
+            e1.record(st)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        stats = lt.lt_ctx_get_stats(ctx, reset=True)
+        lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 0)
+        step_ms = max_over_ranks(statistics.mean(ms), ws, dev)
+        jac = stats["jacobi"]
+        gflops = jac["flops"] / max(jac["ms"], 1e-9) / 1e6
+        peak = FP64_PEAK_GFLOPS if prec == lt.LT_FP64 else FP32_PEAK_GFLOPS
+        leg = {"value": round(job_rate(iters, ws, step_ms), 4), "unit": "iters/s",
+               "ms_per_iter": round(step_ms / iters, 3),
+               "jacobi_ms_per_iter": round(jac["ms"] / max(args.fourier_steps * iters, 1), 3),
+               "roofline": {"kernel": f"jacobi_svt ({label.upper()})", "bound": "alu",
+                            "achieved": round(gflops, 1), "peak": peak, "unit": "GFLOP/s",
+                            "frac": round(gflops / peak, 4),
+                            "peak_source": f"measured {label.upper()} FMA throughput (of measured)"},
+               "rel_residual": rep.rel_residual, "device_status": rep.device_status}
+        if X64 is None:
+            X64 = X.double()
+        else:
+            leg["rel_err_vs_fp64"] = float(torch.linalg.norm(X.double() - X64) / torch.linalg.norm(X64))
+        out[label] = leg
+    if cpu:
+        from oracle import lt_oracle as O  # the cpu_baseline sample only
+        obs_np = obs64.cpu().numpy().reshape(-1).reshape((144, 176, 3, 32), order="F")
+        t0 = time.perf_counter()
+        O.pga(c["mask"], obs_np, c["tau"], c["step"], 2, [O.dct_matrix(32)], fourier=True)
+        dtc = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": round(2 / dtc, 4), "unit": "iters/s",
+                               "cores": os.cpu_count(), "kind": "oracle",
+                               "sample": f"2 TNN-PGA-F iterations of the same problem ({dtc:.1f} s), "
+                                         "numpy complex FFT + LAPACK SVD, FP64"}
+    return out
 
 
 def run_batched_leg(args, dev, ws):
@@ -782,6 +857,10 @@ def main():
                     help="timed calls of the 64-problem batch (0 skips the batched leg)")
     ap.add_argument("--batched-iters", type=int, default=4,
                     help="PGA iterations per call of the 64-problem batch")
+    ap.add_argument("--fourier-steps", type=int, default=2,
+                    help="timed steps of the Fourier-operator (TNN-PGA-F) leg; 0 skips it")
+    ap.add_argument("--fourier-iters", type=int, default=10,
+                    help="PGA iterations per step of the Fourier leg")
     ap.add_argument("--product-steps", type=int, default=5,
                     help="timed calls of the fifth-order product leg (0 skips it)")
     ap.add_argument("--i4", type=int, default=40,

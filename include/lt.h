@@ -54,7 +54,10 @@ typedef enum {
   LT_ERR_TIMEOUT = -5,    /* (device) a bounded wait expired */
   LT_ERR_NONFINITE = -6,  /* (device) NaN or Inf met in a slice */
   LT_ERR_CUDA = -7,       /* a CUDA runtime call failed */
-  LT_ERR_WORKSPACE = -8   /* ws missing, too small or misaligned */
+  LT_ERR_WORKSPACE = -8,  /* ws missing, too small or misaligned */
+  LT_ERR_UNSUPPORTED = -9 /* the call is not defined for this context's operator
+                             (lt_svd, lt_truncate, lt_norms and the PGA objective on a
+                             Fourier context) */
 } lt_status;
 
 /* Bits of the device status word (lt_last_device_status). */
@@ -179,6 +182,27 @@ LT_API lt_status lt_make_cproduct(int64_t n, double* M);
  * number > 1e12), LT_ERR_CUDA.  Needs a current CUDA device. */
 LT_API lt_status lt_ctx_create(int K, const int64_t* mode_sizes, const double* const* M,
                         lt_precision prec, lt_ctx* out);
+
+/* Context of the Fourier operator: M_3 = F_{I3}, the unnormalised DFT of Sec. 2
+ * ((F_n)_{ij} = w^{ij}, w = exp(-2 pi i / n); the t-product for third order), and real
+ * M_4..M_K as in lt_ctx_create (M_rest: host array of K-3 host pointers, ROW-major
+ * doubles; NULL when K = 3).  Tensors stay real; on the transform side mode 3 holds the
+ * coefficients of F_n x in the orthonormal real DFT basis ("slots"), for a tube x of
+ * length n and xh = F_n x:
+ *   slot 0 = xh_0 / sqrt(n);  slots 2k-1, 2k = sqrt(2/n) (Re xh_k, Im xh_k) for
+ *   k = 1..(n-1)/2;  slot n-1 = xh_{n/2} / sqrt(n) for even n
+ * (the other half of xh is the conjugate of the first).  On such a context
+ *   lt_transform / lt_inverse  map a tensor to its slots and back (then modes 4..K);
+ *   lt_product   is A *_L B with M_3 = F: each complex slice product of Algorithm 2;
+ *   lt_svt       thresholds the complex slices of L(A) (n-scaled F) at tau, Algorithm 4;
+ *   lt_pga_complete  is TNN-PGA-F (Sec. 5) with that SVT; continuation is available,
+ *                the objective (LT_OPT_OBJECTIVE) is not (LT_ERR_UNSUPPORTED);
+ *   lt_svd, lt_truncate, lt_norms return LT_ERR_UNSUPPORTED.
+ * LT_MIXED Fourier contexts run the face-wise products on the FP32 SIMT kernel.
+ * Errors: as lt_ctx_create. */
+LT_API lt_status lt_ctx_create_fourier(int K, const int64_t* mode_sizes,
+                                       const double* const* M_rest, lt_precision prec,
+                                       lt_ctx* out);
 LT_API lt_status lt_ctx_destroy(lt_ctx ctx);
 LT_API lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value);
 

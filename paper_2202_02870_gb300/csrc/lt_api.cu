@@ -158,8 +158,7 @@ cudaError_t run_jacobi(Ctx& c, const lt::JacobiPlan& jp, lt::JacobiIO io, cudaSt
   io.flops = c.d_counters + LT_K_JACOBI;
   io.phases = (c.profile && account) ? c.d_counters + 4 : nullptr;
   cudaError_t e = lt::launch_jacobi(c, jp, io, st);
-  // bytes: read the slices, re-read them for the reconstruction, write the result
-  const double n = (double)jp.I1 * jp.I2 * c.P * c.elem;
+  const double n = (double)jp.I1 * jp.I2 * jp.P * c.elem;
   // bytes: read the slices (SVT and truncation re-read them for the reconstruction
   // and write the result; the SVD writes its factors; the singular values alone read)
   sc.done(1, 0.0, jp.mode == lt::JAC_SVD ? 2 * n : (jp.mode == lt::JAC_SIGMA ? n : 3 * n));
@@ -179,11 +178,76 @@ void sweep_retired(Ctx& c) {
   }
 }
 
+// ---- SVT of a Fourier context: real slots and realified pairs (lt_fourier.cu) --------
+struct FourierSvt {
+  lt::FourierSlots f;
+  lt::JacobiPlan jr, jc;              // real slots (I1 x I2), pairs (2 I1 x 2 I2)
+  size_t wr = 0, wc = 0, scratch = 0, total = 0;  // offsets in its workspace region
+};
+
+lt_status fourier_svt_plan(const Ctx& c, int64_t I1, int64_t I2, FourierSvt* F) {
+  F->f = lt::fourier_slots(c);
+  lt_status s = lt::plan_jacobi(c, lt::JAC_SVT, I1, I2, &F->jr, F->f.nreal);
+  if (s != LT_OK) return s;
+  if (F->f.npair > 0 &&
+      (s = lt::plan_jacobi(c, lt::JAC_SVT, 2 * I1, 2 * I2, &F->jc, F->f.npair)) != LT_OK)
+    return s;
+  size_t off = 0;
+  F->wr = off; off += align256((size_t)F->f.nreal * I1 * I2 * c.elem);
+  F->wc = off; off += align256((size_t)F->f.npair * 4 * I1 * I2 * c.elem);
+  F->scratch = off;
+  off += align256(std::max(F->jr.ws_bytes, F->f.npair > 0 ? F->jc.ws_bytes : (size_t)0));
+  F->total = off;
+  return LT_OK;
+}
+
+// The SVT of the complex transform-domain slices at tau (Algorithm 4 with M_3 = F), in
+// place on the slot tensor G: gather, the Jacobi SVT of the real slots at tau / sqrt(n)
+// and of the realified pairs at tau sqrt(2 / n), scatter.  `io` carries the PGA scalars
+// and the per-slice info array (real slots first, then pairs); `region` is F.total bytes.
+cudaError_t run_fourier_svt(Ctx& c, const FourierSvt& F, int64_t I1, int64_t I2, void* G,
+                            double tau, lt::JacobiIO io, void* region, cudaStream_t st,
+                            bool account) {
+  unsigned char* w = static_cast<unsigned char*>(region);
+  void* Wr = w + F.wr;
+  void* Wc = w + F.wc;
+  const double S = (double)I1 * I2, eb = c.elem, n = (double)F.f.n;
+  const double gathered = ((double)F.f.nreal + 4.0 * F.f.npair) * S * eb;
+  cudaError_t e;
+  {
+    Scope sc(c, st, LT_K_AUX, account);
+    e = lt::launch_fourier_realify(c, I1, I2, G, Wr, Wc, io.scal, st);
+    sc.done(1, 0.0, (double)c.P * S * eb + gathered);
+  }
+  io.scratch = w + F.scratch;
+  lt::SliceInfo* info = io.info;
+  if (e == cudaSuccess) {
+    io.A = Wr;
+    io.D = Wr;
+    io.tau = tau / std::sqrt(n);
+    e = run_jacobi(c, F.jr, io, st, account);
+  }
+  if (e == cudaSuccess && F.f.npair > 0) {
+    io.A = Wc;
+    io.D = Wc;
+    io.tau = tau * std::sqrt(2.0 / n);
+    io.info = info ? info + F.f.nreal : nullptr;
+    e = run_jacobi(c, F.jc, io, st, account);
+  }
+  if (e == cudaSuccess) {
+    Scope sc(c, st, LT_K_AUX, account);
+    e = lt::launch_fourier_derealify(c, I1, I2, Wr, Wc, G, io.scal, st);
+    sc.done(1, 0.0, 2.0 * (double)c.P * S * eb);
+  }
+  return e;
+}
+
 // ---- workspace layouts ---------------------------------------------------------------
 struct PgaLayout {
   size_t x2, ghat, partials, scal, info, jac, total;
   lt::TransformPlan fwd, inv;
   lt::JacobiPlan jp;
+  FourierSvt fz;                      // Fourier contexts: the SVT's plans and region
   int max_rows;
 };
 
@@ -193,8 +257,11 @@ lt_status pga_layout(const Ctx& c, int64_t I1, int64_t I2, PgaLayout* L) {
   if (s != LT_OK) return s;
   s = lt::plan_transform(c, I1 * I2, true, &L->inv);
   if (s != LT_OK) return s;
-  s = lt::plan_jacobi(c, lt::JAC_SVT, I1, I2, &L->jp);
-  if (s != LT_OK) return s;
+  if (c.fourier_n) {
+    if ((s = fourier_svt_plan(c, I1, I2, &L->fz)) != LT_OK) return s;
+  } else if ((s = lt::plan_jacobi(c, lt::JAC_SVT, I1, I2, &L->jp)) != LT_OK) {
+    return s;
+  }
   L->max_rows = lt::transform_grid(c, L->inv.pass[L->inv.npass - 1]);
   size_t off = 0;
   L->x2 = off; off += align256((size_t)N * c.elem);
@@ -202,7 +269,7 @@ lt_status pga_layout(const Ctx& c, int64_t I1, int64_t I2, PgaLayout* L) {
   L->partials = off; off += align256((size_t)L->max_rows * 4 * sizeof(double));
   L->scal = off; off += align256(sizeof(lt::PgaScalars));
   L->info = off; off += align256((size_t)c.P * sizeof(lt::SliceInfo));
-  L->jac = off; off += align256(L->jp.ws_bytes);
+  L->jac = off; off += align256(c.fourier_n ? L->fz.total : L->jp.ws_bytes);
   L->total = off;
   return LT_OK;
 }
@@ -246,6 +313,7 @@ const char* lt_status_string(lt_status s) {
     case LT_ERR_NONFINITE: return "non-finite value";
     case LT_ERR_CUDA: return "CUDA runtime error";
     case LT_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+    case LT_ERR_UNSUPPORTED: return "operation not available for this context's operator";
   }
   return "unknown status";
 }
@@ -358,6 +426,25 @@ lt_status lt_ctx_create(int K, const int64_t* mode_sizes, const double* const* M
   return LT_OK;
 }
 
+lt_status lt_ctx_create_fourier(int K, const int64_t* mode_sizes, const double* const* M_rest,
+                                lt_precision prec, lt_ctx* out) {
+  if (out == nullptr) return LT_ERR_ARG;
+  *out = nullptr;
+  if (K < 3 || K - 2 > lt::kMaxModes || mode_sizes == nullptr) return LT_ERR_ARG;
+  if (K > 3 && M_rest == nullptr) return LT_ERR_ARG;
+  const int64_t n = mode_sizes[0];
+  if (n < 1 || n > 4096) return LT_ERR_ARG;
+  // mode 3 in the orthonormal real DFT basis, modes 4..K as given
+  std::vector<double> R((size_t)(n * n));
+  lt::fourier_basis(n, R.data());
+  std::vector<const double*> Ms((size_t)(K - 2));
+  Ms[0] = R.data();
+  for (int q = 1; q < K - 2; ++q) Ms[q] = M_rest[q - 1];
+  const lt_status s = lt_ctx_create(K, mode_sizes, Ms.data(), prec, out);
+  if (s == LT_OK) reinterpret_cast<Ctx*>(*out)->fourier_n = n;
+  return s;
+}
+
 lt_status lt_ctx_destroy(lt_ctx ctx) {
   if (!ctx) return LT_ERR_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
@@ -443,6 +530,7 @@ lt_status lt_workspace_size(lt_ctx ctx, lt_op op, int64_t I1, int64_t I2, int64_
       return LT_OK;
     }
     case LT_OP_SVD: {
+      if (c.fourier_n) return LT_ERR_UNSUPPORTED;
       lt::JacobiPlan jp;
       s = lt::plan_jacobi(c, lt::JAC_SVD, I1, I2, &jp);
       if (s != LT_OK) return s;
@@ -450,6 +538,12 @@ lt_status lt_workspace_size(lt_ctx ctx, lt_op op, int64_t I1, int64_t I2, int64_
       return LT_OK;
     }
     case LT_OP_SVT: {
+      if (c.fourier_n) {
+        FourierSvt F;
+        if ((s = fourier_svt_plan(c, I1, I2, &F)) != LT_OK) return s;
+        *out = F.total;
+        return LT_OK;
+      }
       lt::JacobiPlan jp;
       s = lt::plan_jacobi(c, lt::JAC_SVT, I1, I2, &jp);
       if (s != LT_OK) return s;
@@ -457,6 +551,7 @@ lt_status lt_workspace_size(lt_ctx ctx, lt_op op, int64_t I1, int64_t I2, int64_
       return LT_OK;
     }
     case LT_OP_TRUNCATE: {
+      if (c.fourier_n) return LT_ERR_UNSUPPORTED;
       lt::JacobiPlan jp;
       s = lt::plan_jacobi(c, lt::JAC_TRUNC, I1, I2, &jp);
       if (s != LT_OK) return s;
@@ -464,6 +559,7 @@ lt_status lt_workspace_size(lt_ctx ctx, lt_op op, int64_t I1, int64_t I2, int64_
       return LT_OK;
     }
     case LT_OP_NORMS: {
+      if (c.fourier_n) return LT_ERR_UNSUPPORTED;
       lt::JacobiPlan jp;
       s = lt::plan_jacobi(c, lt::JAC_SIGMA, I1, I2, &jp);
       if (s != LT_OK) return s;
@@ -585,8 +681,13 @@ lt_status lt_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau, 
   if ((s = lt_workspace_size(ctx, LT_OP_SVT, I1, I2, 0, &need)) != LT_OK) return s;
   if ((s = check_ws(ws, ws_bytes, need)) != LT_OK) return s;
   lt::JacobiPlan jp;
+  FourierSvt F;
   lt::TransformPlan pf, pi;
-  if ((s = lt::plan_jacobi(c, lt::JAC_SVT, I1, I2, &jp)) != LT_OK) return s;
+  if (c.fourier_n) {
+    if ((s = fourier_svt_plan(c, I1, I2, &F)) != LT_OK) return s;
+  } else if ((s = lt::plan_jacobi(c, lt::JAC_SVT, I1, I2, &jp)) != LT_OK) {
+    return s;
+  }
   if ((s = lt::plan_transform(c, I1 * I2, false, &pf)) != LT_OK) return s;
   if ((s = lt::plan_transform(c, I1 * I2, true, &pi)) != LT_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
@@ -596,7 +697,9 @@ lt_status lt_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, double tau, 
   io.tau = tau;
   io.scratch = ws;
   cudaError_t e = run_transform(c, pf, I1 * I2, A, D, st);
-  if (e == cudaSuccess) e = run_jacobi(c, jp, io, st);
+  if (e == cudaSuccess)
+    e = c.fourier_n ? run_fourier_svt(c, F, I1, I2, D, tau, io, ws, st, true)
+                    : run_jacobi(c, jp, io, st);
   if (e == cudaSuccess) e = run_transform(c, pi, I1 * I2, D, D, st);
   return cuda_status(e);
 }
@@ -689,6 +792,7 @@ lt_status pga_prepare(Ctx& c, int64_t I1, int64_t I2, const uint8_t* mask, const
                       PgaRun* r) {
   lt_status s = check_dims(I1, I2);
   if (s != LT_OK) return s;
+  if (c.fourier_n && c.objective) return LT_ERR_UNSUPPORTED;
   if ((s = pga_layout(c, I1, I2, &r->L)) != LT_OK) return s;
   if ((s = check_ws(ws, ws_bytes, r->L.total)) != LT_OK) return s;
   unsigned char* w = static_cast<unsigned char*>(ws);
@@ -757,7 +861,10 @@ cudaError_t pga_iteration(PgaRun& r, int64_t j, cudaStream_t st, bool account) {
     e = lt::launch_transform(c, r.L.fwd, nullptr, r.Gh, lt::FUSE_PGA_FORWARD, &r.f, st, nullptr);
     sc.done(r.L.fwd.npass, r.fwd_flops, r.fwd_bytes);
   }
-  if (e == cudaSuccess) e = run_jacobi(c, r.L.jp, r.io, st, account);
+  if (e == cudaSuccess)
+    e = c.fourier_n ? run_fourier_svt(c, r.L.fz, r.I1, r.I2, r.Gh, r.io.tau, r.io, r.io.scratch,
+                                      st, account)
+                    : run_jacobi(c, r.L.jp, r.io, st, account);
   if (e == cudaSuccess) {
     Scope sc(c, st, LT_K_TRANSFORM, account);
     e = lt::launch_transform(c, r.L.inv, r.Gh, r.Gh, lt::FUSE_PGA_INVERSE, &r.f, st, &rows);
@@ -765,7 +872,8 @@ cudaError_t pga_iteration(PgaRun& r, int64_t j, cudaStream_t st, bool account) {
   }
   if (e == cudaSuccess) {
     Scope sc(c, st, LT_K_AUX, account);
-    e = lt::launch_pga_finish(r.scal, r.f.partials, rows, r.io.info, c.P, r.tau, c.objective,
+    const int64_t slices = c.fourier_n ? r.L.fz.f.nreal + r.L.fz.f.npair : c.P;
+    e = lt::launch_pga_finish(r.scal, r.f.partials, rows, r.io.info, slices, r.tau, c.objective,
                               c.d_status, st);
     sc.done(1, 0.0, 0.0);
   }
@@ -778,9 +886,18 @@ void pga_account_iteration(PgaRun& r) {
   c.stats.k[LT_K_TRANSFORM].launches += r.L.fwd.npass + r.L.inv.npass;
   c.stats.k[LT_K_TRANSFORM].flops += r.fwd_flops + r.inv_flops;
   c.stats.k[LT_K_TRANSFORM].bytes += r.fwd_bytes + r.inv_bytes;
-  c.stats.k[LT_K_JACOBI].launches += 1;
-  c.stats.k[LT_K_JACOBI].bytes += 3.0 * (double)r.I1 * r.I2 * c.P * c.elem;
-  c.stats.k[LT_K_AUX].launches += 1;
+  const double S = (double)r.I1 * r.I2 * c.elem;
+  if (c.fourier_n) {
+    const lt::FourierSlots& f = r.L.fz.f;
+    c.stats.k[LT_K_JACOBI].launches += 1 + (f.npair > 0);
+    c.stats.k[LT_K_JACOBI].bytes += 3.0 * ((double)f.nreal + 4.0 * f.npair) * S;
+    c.stats.k[LT_K_AUX].launches += 3;
+    c.stats.k[LT_K_AUX].bytes += 3.0 * (double)c.P * S + ((double)f.nreal + 4.0 * f.npair) * S;
+  } else {
+    c.stats.k[LT_K_JACOBI].launches += 1;
+    c.stats.k[LT_K_JACOBI].bytes += 3.0 * (double)c.P * S;
+    c.stats.k[LT_K_AUX].launches += 1;
+  }
 }
 
 cudaError_t pga_end(PgaRun& r, lt_pga_state* state, lt_pga_report* report, cudaStream_t st) {

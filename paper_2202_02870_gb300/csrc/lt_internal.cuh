@@ -43,6 +43,9 @@ struct Ctx {
   double mu0 = 0.0;                   // PGA continuation: mu_0 (0 = off)
   double nu = 0.9;                    // PGA continuation: decay of mu
   mutable int64_t tc_launches = 0;    // tensor-core kernel launches (lt_ctx_get_stats)
+  // Fourier operator (M_3 = F_{I3}): 0 for a real context, else I3.  Mode 3 is then
+  // stored as the orthonormal real DFT basis (see lt_fourier.cu for the slot layout).
+  int64_t fourier_n = 0;
   // LT_MIXED: the transform matrices as tensor-core B operands, B(k, n) = M(n, k) at
   // k + n * ld (ld = I rounded up to 4, zero padded), each at a 16-byte aligned offset.
   float* d_tc_fwd = nullptr;
@@ -181,7 +184,9 @@ struct SliceInfo {          // per slice, written by the Jacobi kernel
   double nuclear;           // sum of the shrunk singular values
 };
 
-lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan* jp);
+// count: slices to process (default: the context's P).
+lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan* jp,
+                      int64_t count = -1);
 
 struct JacobiIO {
   const void* A = nullptr;  // input slices (transform domain)
@@ -217,6 +222,29 @@ cudaError_t launch_copy_bytes(void* dst, const void* src, size_t bytes, cudaStre
 // max(I1, I2) * u * max sigma.
 cudaError_t launch_norms_finish(const void* sigma, int elem, int64_t P, int n, double rank_tol,
                                 double* out, int32_t* multirank, cudaStream_t st);
+// ----------------------------------------------------------------------------------
+// Fourier operator (lt_fourier.cu).  Slots of a mode-3 tube of length n: 0 = DC, then
+// (2k-1, 2k) = the real and imaginary parts of the k-th conjugate pair (k = 1..(n-1)/2),
+// and n-1 = Nyquist for even n.  Real slots and realified pairs are gathered into
+// separate slice sets for the Jacobi SVT and scattered back.
+// ----------------------------------------------------------------------------------
+struct FourierSlots {
+  int64_t n = 0, R = 0;     // tube length, tubes (P / n)
+  int64_t nreal = 0;        // real slots: R (odd n) or 2R (even n)
+  int64_t npair = 0;        // conjugate pairs: R (n - 1) / 2
+};
+FourierSlots fourier_slots(const Ctx& c);
+// Wr: nreal slices I1 x I2; Wc: npair slices 2 I1 x 2 I2 holding [[a1, -a2], [a2, a1]].
+cudaError_t launch_fourier_realify(const Ctx& c, int64_t I1, int64_t I2, const void* G,
+                                   void* Wr, void* Wc, const PgaScalars* scal,
+                                   cudaStream_t st);
+// The real slots from Wr, the pairs from the left block column of Wc.
+cudaError_t launch_fourier_derealify(const Ctx& c, int64_t I1, int64_t I2, const void* Wr,
+                                     const void* Wc, void* G, const PgaScalars* scal,
+                                     cudaStream_t st);
+// Orthonormal real DFT basis of length n, row-major n x n doubles (host).
+void fourier_basis(int64_t n, double* R);
+
 cudaError_t launch_select_result(const PgaScalars* scal, void* x_user, const void* x_alt,
                                  void* x_prev_out, size_t bytes, cudaStream_t st);
 

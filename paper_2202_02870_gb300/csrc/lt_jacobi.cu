@@ -493,12 +493,13 @@ size_t svt_smem(const JacobiPlan& jp) {
 
 }  // namespace
 
-lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan* out) {
+lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan* out,
+                      int64_t count) {
   JacobiPlan jp;
   jp.mode = mode;
   jp.I1 = I1;
   jp.I2 = I2;
-  jp.P = c.P;
+  jp.P = count >= 0 ? count : c.P;
   jp.transposed = I1 < I2;
   jp.m = (int)std::max(I1, I2);
   jp.n = (int)std::min(I1, I2);

@@ -21,7 +21,8 @@ LIB_PATH = os.path.join(_HERE, "liblt.so")
 LT_OK = 0
 STATUS = {0: "LT_OK", -1: "LT_ERR_ARG", -2: "LT_ERR_SHAPE", -3: "LT_ERR_SINGULAR",
           -4: "LT_ERR_NOCONV", -5: "LT_ERR_TIMEOUT", -6: "LT_ERR_NONFINITE",
-          -7: "LT_ERR_CUDA", -8: "LT_ERR_WORKSPACE"}
+          -7: "LT_ERR_CUDA", -8: "LT_ERR_WORKSPACE", -9: "LT_ERR_UNSUPPORTED"}
+STATUS_CODE = {name: code for code, name in STATUS.items()}
 LT_DEV_NOCONV, LT_DEV_NONFINITE, LT_DEV_TIMEOUT = 1, 2, 4
 LT_FP64, LT_FP32, LT_MIXED = 0, 1, 2
 (LT_OP_TRANSFORM, LT_OP_INVERSE, LT_OP_PRODUCT, LT_OP_SVD, LT_OP_SVT, LT_OP_PGA, LT_OP_TRUNCATE,
@@ -67,6 +68,9 @@ SIGNATURES = {
     "lt_make_cproduct": (C.c_int, [_i64, C.POINTER(C.c_double)]),
     "lt_ctx_create": (C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.POINTER(C.c_double)),
                                 C.c_int, C.POINTER(C.c_void_p)]),
+    "lt_ctx_create_fourier": (C.c_int, [C.c_int, C.POINTER(C.c_int64),
+                                        C.POINTER(C.POINTER(C.c_double)), C.c_int,
+                                        C.POINTER(C.c_void_p)]),
     "lt_ctx_destroy": (C.c_int, [_vp]),
     "lt_ctx_set_option": (C.c_int, [_vp, C.c_int, _dbl]),
     "lt_workspace_size": (C.c_int, [_vp, C.c_int, _i64, _i64, _i64, C.POINTER(C.c_size_t)]),
@@ -159,15 +163,23 @@ class Context:
     """Owns an lt_ctx (the operator L with matrices M_3..M_K)."""
 
     def __init__(self, mode_sizes: Sequence[int], matrices: Sequence[np.ndarray],
-                 precision: int = LT_FP64):
+                 precision: int = LT_FP64, fourier: bool = False):
+        """fourier=True: M_3 = F_{I3} (lt_ctx_create_fourier) and `matrices` holds
+        M_4..M_K only."""
         sizes = (C.c_int64 * len(mode_sizes))(*[int(s) for s in mode_sizes])
         self._mats = [np.ascontiguousarray(m, dtype=np.float64) for m in matrices]
-        ptrs = (C.POINTER(C.c_double) * len(self._mats))(
+        ptrs = (C.POINTER(C.c_double) * max(1, len(self._mats)))(
             *[m.ctypes.data_as(C.POINTER(C.c_double)) for m in self._mats])
         h = C.c_void_p()
-        _check("lt_ctx_create", lib().lt_ctx_create(len(mode_sizes) + 2, sizes, ptrs,
-                                                    int(precision), C.byref(h)))
+        if fourier:
+            _check("lt_ctx_create_fourier", lib().lt_ctx_create_fourier(
+                len(mode_sizes) + 2, sizes, ptrs if self._mats else None, int(precision),
+                C.byref(h)))
+        else:
+            _check("lt_ctx_create", lib().lt_ctx_create(len(mode_sizes) + 2, sizes, ptrs,
+                                                        int(precision), C.byref(h)))
         self.handle = h
+        self.fourier = bool(fourier)
         self.mode_sizes = tuple(int(s) for s in mode_sizes)
         self.precision = int(precision)
         self.P = int(np.prod(self.mode_sizes))
@@ -191,6 +203,11 @@ class Context:
 
 def lt_ctx_create(mode_sizes, matrices, precision=LT_FP64) -> Context:
     return Context(mode_sizes, matrices, precision)
+
+
+def lt_ctx_create_fourier(mode_sizes, matrices_rest=(), precision=LT_FP64) -> Context:
+    """Context of the Fourier operator: M_3 = F_{I3}, M_4.. = matrices_rest."""
+    return Context(mode_sizes, matrices_rest, precision, fourier=True)
 
 
 def lt_ctx_destroy(ctx: Context):
