@@ -567,6 +567,7 @@ def run_case(args):
     ctx = lt.Context([3, 32], [lt.lt_make_dct(3), lt.lt_make_dct(32)], prec)
     lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_GROUP, args.jacobi_group)
     lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_BLOCK, args.jacobi_pairwise)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_CLUSTER, args.jacobi_cluster)
     if args.case == "svt":
         G = to_dev(c["mask"] * np.random.default_rng(1).standard_normal(c["mask"].shape))
         D = torch.empty_like(G)
@@ -592,6 +593,7 @@ def run_case(args):
     ms = e0.elapsed_time(e1) / args.steps
     print(json.dumps({"case": args.case, "precision": args.precision,
                       "jacobi_group": args.jacobi_group, "jacobi_pairwise": args.jacobi_pairwise,
+                      "jacobi_cluster": args.jacobi_cluster,
                       "ms_per_call": ms,
                       f"{unit}_per_s": units / (ms / 1e3)}))
 
@@ -878,6 +880,8 @@ def main():
     ap.add_argument("--jacobi-pairwise", type=int, default=0, choices=[0, 1, 2],
                     help="1: rotate column pairs straight through shared memory (no "
                          "register blocks)")
+    ap.add_argument("--jacobi-cluster", type=int, default=0, choices=[0, 1, 3, 4],
+                    help="--case svt: SVT kernel form (LT_OPT_JACOBI_CLUSTER)")
     ap.add_argument("--jacobi-group", type=int, default=0, choices=[0, 8, 16, 32],
                     help="lanes per Jacobi column pair (0: the planner's choice)")
     args = ap.parse_args()

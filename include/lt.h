@@ -120,7 +120,11 @@ typedef enum {
                                 the start of the run, checkpoints included) thresholds at
                                 step * max(nu^k mu_0, tau).  0 (default) = off, fixed tau.
                                 Not available in lt_pga_complete_batched (LT_ERR_ARG). */
-  LT_OPT_NU = 9              /* PGA continuation decay nu, 0 < nu <= 1 (default 0.9) */
+  LT_OPT_NU = 9,             /* PGA continuation decay nu, 0 < nu <= 1 (default 0.9) */
+  LT_OPT_JACOBI_CLUSTER = 10 /* SVT kernel form: 0 = planner's choice (default), 1 = one
+                                CTA per slice, 3 or 4 = a thread-block cluster of that many
+                                CTAs per slice (columns spread over the CTAs' shared
+                                memory; slices up to 288 columns after padding) */
 } lt_option;
 
 /* Kernel families counted by lt_ctx_get_stats. */

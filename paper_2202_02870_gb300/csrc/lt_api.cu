@@ -485,6 +485,10 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
       if (!(value == 0 || value == 1 || value == 2)) return LT_ERR_ARG;
       c->jacobi_pairwise = (int)value;
       return LT_OK;
+    case LT_OPT_JACOBI_CLUSTER:
+      if (!(value == 0 || value == 1 || value == 3 || value == 4)) return LT_ERR_ARG;
+      c->jacobi_cluster = (int)value;
+      return LT_OK;
     case LT_OPT_JACOBI_GROUP:
       if (!(value == 0 || value == 8 || value == 16 || value == 32)) return LT_ERR_ARG;
       c->jacobi_group = (int)value;

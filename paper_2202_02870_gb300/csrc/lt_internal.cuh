@@ -37,6 +37,8 @@ struct Ctx {
   int objective = 0;
   int jacobi_group = 0;               // 0: planner's choice
   int jacobi_pairwise = 0;            // 1: no register blocking
+  int jacobi_cluster = 0;             // SVT: 0 = planner's choice, 1 = one CTA per slice,
+                                      // 3 or 4 = that many CTAs per slice (a cluster)
   int tc_mode_min = 64;               // LT_MIXED: modes of at least this size (and not
                                       // mode 3) run as tensor-core passes; 0 = never
   int tc_tile_n = 0;                  // LT_MIXED: forced tensor-core tile width (0 = auto)
@@ -176,6 +178,8 @@ struct JacobiPlan {
   int threads = 512;
   int smem = 0;
   size_t ws_bytes = 0;                  // scratch bytes (global W, Jacobi V, info)
+  int cluster = 0;                      // > 1: CTAs per slice (cluster form of the SVT)
+  int elem = 8;                         // bytes per element
 };
 
 struct SliceInfo {          // per slice, written by the Jacobi kernel

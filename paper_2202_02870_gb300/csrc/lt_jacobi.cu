@@ -416,6 +416,7 @@ cudaError_t launch_t(const JArgs& a, int grid, cudaStream_t st) {
 }
 
 int jacobi_grid(const Ctx& c, const JacobiPlan& jp) {
+  if (jp.cluster > 1) return jp.cluster * (int)std::min<int64_t>(jp.P, 1 << 18);
   if (jp.w_in_smem && jp.mode != JAC_SVD) return (int)std::min<int64_t>(jp.P, 1 << 20);
   // global regions are per CTA: bound the grid by what can be resident
   return (int)std::max<int64_t>(1, std::min<int64_t>(jp.P, (int64_t)c.sms * 2));
@@ -493,6 +494,55 @@ size_t svt_smem(const JacobiPlan& jp) {
 
 }  // namespace
 
+// The cluster form of the SVT kernel (lt_jacobi_cluster.cuh) with C CTAs per slice:
+// columns padded to a multiple of 2C, C-th of them per CTA, all in shared memory.
+bool cluster_plan(const Ctx& c, JacobiPlan* jp, int C) {
+  const int np = (jp->n + 2 * C - 1) / (2 * C) * (2 * C);
+  const int G = 16;
+  int E;
+  if (np <= 96) E = 6;
+  else if (np <= 144) E = 9;
+  else if (np <= 192) E = 12;
+  else if (np <= 288) E = 18;
+  else return false;
+  JacobiPlan q = *jp;
+  q.cluster = C;
+  q.G = G;
+  q.E = E;
+  q.B = 1;
+  q.npad = np;
+  q.w_in_smem = true;
+  const int base = std::max(q.m, 32 * ((G * E + 31) / 32));
+  q.ld = base | 1;
+  const int nl = np / C, ppw = 32 / G, mine = (np / 2 + C - 1) / C;
+  const int maxw = jac::cluster_max_threads(c.elem, E) / 32;
+  q.threads = 32 * std::max(4, std::min(maxw, (mine + ppw - 1) / ppw));
+  const size_t need = (size_t)c.elem * ((size_t)q.ld * nl + 4 * (size_t)nl + q.ld + np) +
+                      sizeof(int) * ((size_t)nl + 2 * (size_t)np);
+  // the kernel's static shared memory (per-pair scalars, slots) takes up to ~4 KB
+  if (need > (size_t)kSmemOptin - 6144) return false;
+  q.smem = (int)((need + 15) & ~size_t(15));
+  q.ws_bytes = 0;
+  jac::JArgs a;
+  a.jp = q;
+  if (!jac::svt_cluster_resident(a)) return false;
+  *jp = q;
+  return true;
+}
+
+// Relative time of the SVT launch, counted in slice-times of one CTA on an SM of its
+// own: the one-CTA form runs ceil(P / SMs) rounds of slices (4x slower per slice when
+// its working matrix is in global memory); the cluster form gives each SM
+// ceil(P C / SMs) CTAs of 1/C of a slice each, at 1.5x the one-CTA time per column pair
+// (its barriers and remote accesses; measured on 144 x 176 FP64 slices: 96 slices on
+// clusters of 3 take as long as on single CTAs, 2/3 of an SM each).
+double svt_cost(const Ctx& c, const JacobiPlan& jp) {
+  const double sms = c.sms;
+  if (jp.cluster > 1)
+    return std::ceil((double)jp.P * jp.cluster / sms) / jp.cluster * 1.5;
+  return std::ceil((double)jp.P / sms) * (jp.w_in_smem ? 1.0 : 4.0);
+}
+
 lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan* out,
                       int64_t count) {
   JacobiPlan jp;
@@ -506,6 +556,13 @@ lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan
   jp.npad = jp.n + (jp.n & 1);
   jp.threads = kJThreads;
   jp.w_in_smem = true;
+  jp.elem = c.elem;
+  if (mode == JAC_SVT && (c.jacobi_cluster == 3 || c.jacobi_cluster == 4)) {
+    // forced cluster form
+    if (!cluster_plan(c, &jp, c.jacobi_cluster)) return LT_ERR_SHAPE;
+    *out = jp;
+    return LT_OK;
+  }
   size_t need;
   if (mode != JAC_SVD) {
     // QR-preconditioned kernel: Jacobi on the n x n factor R^T, G lanes per column
@@ -563,6 +620,18 @@ lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan
   if (!jp.w_in_smem) ws += (size_t)c.elem * grid * jp.ld * jp.npad;
   if (mode == JAC_SVD) ws += (size_t)c.elem * grid * jp.npad * jp.npad;
   jp.ws_bytes = (ws + 255) & ~size_t(255);
+  if (mode == JAC_SVT && c.jacobi_cluster == 0 && c.jacobi_group == 0 && c.jacobi_pairwise == 0 &&
+      (c.elem == 8 || !jp.w_in_smem)) {
+    // planner's choice between one CTA and a cluster per slice (FP32: only against the
+    // global-memory form; the register-blocked one-CTA FP32 sweeps do more per cycle
+    // than the cluster form's pairwise ones)
+    JacobiPlan best = jp;
+    for (int C : {3, 4}) {
+      JacobiPlan q = jp;
+      if (cluster_plan(c, &q, C) && svt_cost(c, q) < svt_cost(c, best)) best = q;
+    }
+    jp = best;
+  }
   *out = jp;
   return LT_OK;
 }
@@ -585,6 +654,7 @@ cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io
                            : (c.elem == 8 ? rows * u : std::max(std::sqrt(rows) / 8.0, 4.0) * u);
   a.status = c.d_status;
   const int grid = jacobi_grid(c, jp);
+  if (jp.cluster > 1) return jac::launch_svt_cluster(a, grid, st);
   if (jp.mode != JAC_SVD) {
     // try the translation units in turn; each returns cudaErrorNotSupported for shapes
     // it does not hold

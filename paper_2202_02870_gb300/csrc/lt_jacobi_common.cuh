@@ -139,6 +139,17 @@ cudaError_t launch_svt_f64_a(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f64_b(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f64_c(const JArgs& a, int grid, cudaStream_t st);
 // Instantiated (G, B, E) shapes (rows padded to G E): see svt_shape in lt_jacobi.cu.
+// Cluster form (lt_jacobi_cl.cu): jp.cluster CTAs per slice; grid = jp.cluster x slices.
+cudaError_t launch_svt_cluster(const JArgs& a, int grid, cudaStream_t st);
+// Thread cap and minimum resident CTAs of a cluster-form instantiation (16 lanes per
+// pair, E rows per lane): up to 12 rows per lane two CTAs of 384 threads share an SM
+// (85 registers each); 18 rows per lane keep one CTA of up to 576 (FP64) or 768 (FP32).
+constexpr int cluster_max_threads(int elem, int E) {
+  return E <= 12 ? 384 : (elem == 8 ? kMaxThreadsF64 : kMaxThreadsF32);
+}
+constexpr int cluster_min_blocks(int E) { return E <= 12 ? 2 : 1; }
+// At least one cluster of the plan's shape can be resident on the device.
+bool svt_cluster_resident(const JArgs& a);
 
 }  // namespace jac
 }  // namespace lt
