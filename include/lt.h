@@ -121,10 +121,13 @@ typedef enum {
                                 step * max(nu^k mu_0, tau).  0 (default) = off, fixed tau.
                                 Not available in lt_pga_complete_batched (LT_ERR_ARG). */
   LT_OPT_NU = 9,             /* PGA continuation decay nu, 0 < nu <= 1 (default 0.9) */
-  LT_OPT_JACOBI_CLUSTER = 10 /* SVT kernel form: 0 = planner's choice (default), 1 = one
-                                CTA per slice, 3 or 4 = a thread-block cluster of that many
-                                CTAs per slice (columns spread over the CTAs' shared
-                                memory; slices up to 288 columns after padding) */
+  LT_OPT_JACOBI_CLUSTER = 10 /* SVT kernel form: 0 = planner's choice (default; FP64:
+                                a cluster when the launch's slices leave SMs idle or do
+                                not fit one CTA's shared memory, counted as if the launch
+                                had the GPU to itself), 1 = one CTA per slice, 3 or 4 = a
+                                thread-block cluster of that many CTAs per slice (columns
+                                spread over the CTAs' shared memory; slices up to 288
+                                columns after padding) */
 } lt_option;
 
 /* Kernel families counted by lt_ctx_get_stats. */

@@ -621,10 +621,11 @@ lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan
   if (mode == JAC_SVD) ws += (size_t)c.elem * grid * jp.npad * jp.npad;
   jp.ws_bytes = (ws + 255) & ~size_t(255);
   if (mode == JAC_SVT && c.jacobi_cluster == 0 && c.jacobi_group == 0 && c.jacobi_pairwise == 0 &&
-      (c.elem == 8 || !jp.w_in_smem)) {
-    // planner's choice between one CTA and a cluster per slice (FP32: only against the
-    // global-memory form; the register-blocked one-CTA FP32 sweeps do more per cycle
-    // than the cluster form's pairwise ones)
+      c.elem == 8) {
+    // planner's choice between one CTA and a cluster per slice, FP64 only: the FP32
+    // cluster form (pairwise rotations) measured 2.6x slower than the register-blocked
+    // one-CTA sweeps on 144 x 176 slices, and in a batch of problems, whose other
+    // launches fill the SMs, slower than the global-memory one-CTA form too
     JacobiPlan best = jp;
     for (int C : {3, 4}) {
       JacobiPlan q = jp;
