@@ -60,7 +60,8 @@ ORACLE_ITERS_PER_STEP = 3
 # the files still hash the same (else null: the counters describe another kernel).
 JACOBI_FP64_SOURCES = [f"paper_2202_02870_gb300/csrc/{f}" for f in (
     "lt_jacobi_svt.cuh", "lt_jacobi_common.cuh", "lt_internal.cuh", "lt_jacobi.cu",
-    "lt_jacobi_f64_a.cu", "lt_jacobi_f64_b.cu", "lt_jacobi_f64_c.cu")]
+    "lt_jacobi_f64_a.cu", "lt_jacobi_f64_b.cu", "lt_jacobi_f64_c.cu",
+    "lt_jacobi_cluster.cuh", "lt_jacobi_cl.cu")]
 
 
 def sources_sha256(files):

@@ -495,9 +495,11 @@ size_t svt_smem(const JacobiPlan& jp) {
 }  // namespace
 
 // The cluster form of the SVT kernel (lt_jacobi_cluster.cuh) with C CTAs per slice:
-// columns padded to a multiple of 2C, C-th of them per CTA, all in shared memory.
+// columns padded to a multiple of 4C (2C half-blocks of an even number of columns), a
+// C-th of them per CTA, all in shared memory.
 bool cluster_plan(const Ctx& c, JacobiPlan* jp, int C) {
-  const int np = (jp->n + 2 * C - 1) / (2 * C) * (2 * C);
+  // 2C half-blocks of an even number of columns
+  const int np = (jp->n + 4 * C - 1) / (4 * C) * (4 * C);
   const int G = 16;
   int E;
   if (np <= 96) E = 6;
@@ -514,7 +516,7 @@ bool cluster_plan(const Ctx& c, JacobiPlan* jp, int C) {
   q.w_in_smem = true;
   const int base = std::max(q.m, 32 * ((G * E + 31) / 32));
   q.ld = base | 1;
-  const int nl = np / C, ppw = 32 / G, mine = (np / 2 + C - 1) / C;
+  const int nl = np / C, ppw = 32 / G, mine = nl / 2;  // pairs per local round
   const int maxw = jac::cluster_max_threads(c.elem, E) / 32;
   q.threads = 32 * std::max(4, std::min(maxw, (mine + ppw - 1) / ppw));
   const size_t need = (size_t)c.elem * ((size_t)q.ld * nl + 4 * (size_t)nl + q.ld + np) +
@@ -533,13 +535,14 @@ bool cluster_plan(const Ctx& c, JacobiPlan* jp, int C) {
 // Relative time of the SVT launch, counted in slice-times of one CTA on an SM of its
 // own: the one-CTA form runs ceil(P / SMs) rounds of slices (4x slower per slice when
 // its working matrix is in global memory); the cluster form gives each SM
-// ceil(P C / SMs) CTAs of 1/C of a slice each, at 1.5x the one-CTA time per column pair
-// (its barriers and remote accesses; measured on 144 x 176 FP64 slices: 96 slices on
-// clusters of 3 take as long as on single CTAs, 2/3 of an SM each).
+// ceil(P C / SMs) CTAs of 1/C of a slice each, at 1.25x the one-CTA time per column pair
+// (the half-block moves, barriers and two CTAs sharing an SM; measured on 96 FP64 slices
+// of 144 x 176: 16.3 ms on clusters of 3, 19.9 ms on clusters of 4, 19.8 ms on single
+// CTAs).
 double svt_cost(const Ctx& c, const JacobiPlan& jp) {
   const double sms = c.sms;
   if (jp.cluster > 1)
-    return std::ceil((double)jp.P * jp.cluster / sms) / jp.cluster * 1.5;
+    return std::ceil((double)jp.P * jp.cluster / sms) / jp.cluster * 1.25;
   return std::ceil((double)jp.P / sms) * (jp.w_in_smem ? 1.0 : 4.0);
 }
 
@@ -622,10 +625,10 @@ lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan
   jp.ws_bytes = (ws + 255) & ~size_t(255);
   if (mode == JAC_SVT && c.jacobi_cluster == 0 && c.jacobi_group == 0 && c.jacobi_pairwise == 0 &&
       c.elem == 8) {
-    // planner's choice between one CTA and a cluster per slice, FP64 only: the FP32
-    // cluster form (pairwise rotations) measured 2.6x slower than the register-blocked
-    // one-CTA sweeps on 144 x 176 slices, and in a batch of problems, whose other
-    // launches fill the SMs, slower than the global-memory one-CTA form too
+    // planner's choice between one CTA and a cluster per slice, FP64 only (FP32 keeps
+    // the register-blocked one-CTA sweeps unless the cluster form is forced: the model
+    // counts a launch as if it had the GPU to itself, which batches of FP32 problems,
+    // whose other launches fill the SMs, contradicted)
     JacobiPlan best = jp;
     for (int C : {3, 4}) {
       JacobiPlan q = jp;

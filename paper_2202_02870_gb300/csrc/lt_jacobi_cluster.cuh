@@ -12,9 +12,10 @@
 //   QR      step j: each CTA proposes its best pivot; the owner of column j swaps and
 //           forms the Householder vector; every CTA copies the vector and updates its
 //           own columns (two cluster barriers per step).
-//   Jacobi  pair k of a round is handled by CTA k mod C (reading and writing the two
-//           columns wherever they live); a cluster barrier closes each round, so every
-//           column is touched by one pair at a time.  Sweeps end when no CTA rotated.
+//   Jacobi  parallel block Jacobi: two half-blocks of columns per CTA, all pairs between
+//           and (once per sweep) inside them rotated in the CTA's own shared memory,
+//           then the half-blocks move on a round-robin tournament of the 2C half-blocks
+//           (cluster barriers only around the moves).  Sweeps end when no CTA rotated.
 //   Recon.  CTA r computes the rows r, r + C, ... of the result, reading the kept
 //           columns of Z from their owners.
 // No remote atomics: per-CTA values (pivot candidates, maxima, flags, counts) go to
@@ -333,137 +334,193 @@ jacobi_svt_cluster_kernel(const JArgs a) {
         }
       }
     };
+    // Parallel block Jacobi: the local columns of a CTA are two half-blocks of h columns
+    // (slots 0 and 1).  A sweep is 2C - 1 block rounds of a round-robin tournament on the
+    // 2C half-blocks; in block round b, CTA k holds the two half-blocks the tournament
+    // pairs at position k and rotates every pair between them (h local rounds of h
+    // disjoint pairs), plus, in the first block round, the pairs inside each of them
+    // (h - 1 local rounds).  Local rounds touch only the CTA's own shared memory; between
+    // block rounds the half-blocks move to their next holders through distributed shared
+    // memory.  Every pair of columns meets once per sweep.
     int sweeps = 0, nrot = 0;
     bool rotated = true;
-    const int npairs = np / 2, cfix = np - 1;
-    const int mine = (npairs - rank + C - 1) / C;  // pairs k = kl C + rank
+    const int h = nl / 2;
+    constexpr int NB = 2 * C;
+    auto held = [&](int b, int k, int sl) { return sl == 0 ? rr_i(b, k, NB) : rr_j(b, k, NB); };
+    // local columns (i, j) of pair kq in local round lr of block round b
+    auto pair_of = [&](int b, int lr, int kq, int& i, int& j) {
+      if (b == 0 && lr < h - 1) {  // inside each half-block: h / 2 pairs in each slot
+        const int sl = kq < h / 2 ? 0 : 1, kk = kq - sl * (h / 2);
+        i = sl * h + rr_i(lr, kk, h);
+        j = sl * h + rr_j(lr, kk, h);
+      } else {                     // across the two half-blocks
+        const int sh = b == 0 ? lr - (h - 1) : lr;
+        i = kq;
+        j = h + (kq + sh) % h;
+      }
+    };
     while (rotated && sweeps < a.max_sweeps) {
       column_norms();
-      cl.sync();
+      __syncthreads();
       int flag = 0;
-      for (int rnd = 0; rnd < cfix; ++rnd) {
-        for (int k0 = 0; k0 < mine; k0 += ngrp) {
-          const int kl = k0 + grp;
-          const bool active = kl < mine;
-          int i = 0, j = 0;
-          if (active) {
-            const int k = kl * C + rank;
-            if (k == 0) {
-              i = cfix;
-              j = rnd;
+      for (int b = 0; b < NB - 1; ++b) {
+        const int nlr = (b == 0 ? h - 1 : 0) + h;
+        for (int lr = 0; lr < nlr; ++lr) {
+          for (int k0 = 0; k0 < h; k0 += ngrp) {
+            const int kq = k0 + grp;
+            const bool active = kq < h;
+            int i = 0, j = 0;
+            if (active) pair_of(b, lr, kq, i, j);
+            T* ci = Wl + (size_t)ld * i;
+            T* cj = Wl + (size_t)ld * j;
+            T x[E], y[E];
+            T g = T(0);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              x[e] = active ? ci[gl + G * e] : T(0);
+              y[e] = active ? cj[gl + G * e] : T(0);
+              g = fma(x[e], y[e], g);
+            }
+            g = group_sum<G>(g);
+            if constexpr (kScaled) {
+              // scaled rotations in three phases, as in jacobi_svt_kernel
+              if (gl == 0) s_pg[grp] = g;
+              __syncthreads();
+              const int batch = min(ngrp, h - k0);
+              for (int q = threadIdx.x; q < batch; q += blockDim.x) {
+                int pi, pj;
+                pair_of(b, lr, k0 + q, pi, pj);
+                const T al = nrm2[pi], be = nrm2[pj];
+                const T di = dsc[pi], dj = dsc[pj];
+                const T gq = s_pg[q] * (di * dj);
+                int rot = 0;
+                if (al > T(0) && be > T(0) && gq * gq > tol2 * al * be) {
+                  T cs, ic, t;
+                  rotation_scaled(al, be, gq, cs, ic, t);
+                  const T ei = isc[pi], ej = isc[pj];
+                  T di2 = di * cs, dj2 = dj * cs, ei2 = ei * ic, ej2 = ej * ic;
+                  s_pa[q] = t * dj * ei;
+                  s_pb[q] = t * di * ej;
+                  T fx = T(1), fy = T(1);
+                  if (di2 < T(0x1p-64)) { fx = di2; di2 = ei2 = T(1); }
+                  if (dj2 < T(0x1p-64)) { fy = dj2; dj2 = ej2 = T(1); }
+                  s_sx[q] = fx;
+                  s_sy[q] = fy;
+                  nrm2[pi] = al - t * gq;
+                  nrm2[pj] = be + t * gq;
+                  dsc[pi] = di2;
+                  dsc[pj] = dj2;
+                  isc[pi] = ei2;
+                  isc[pj] = ej2;
+                  ++nrot;
+                  flag = 1;
+                  rot = 1;
+                }
+                s_pr[q] = rot;
+              }
+              __syncthreads();
+              if (active && s_pr[grp]) {
+                const T alpha = s_pa[grp], beta = s_pb[grp];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                  const T xe = x[e], ye = y[e];
+                  x[e] = fma(-alpha, ye, xe);
+                  y[e] = fma(beta, xe, ye);
+                }
+                const T fx = s_sx[grp], fy = s_sy[grp];
+                if (fx != T(1)) {
+#pragma unroll
+                  for (int e = 0; e < E; ++e) x[e] *= fx;
+                }
+                if (fy != T(1)) {
+#pragma unroll
+                  for (int e = 0; e < E; ++e) y[e] *= fy;
+                }
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                  ci[gl + G * e] = x[e];
+                  cj[gl + G * e] = y[e];
+                }
+              }
             } else {
-              i = rnd + k;
-              if (i >= cfix) i -= cfix;
-              j = rnd - k;
-              if (j < 0) j += cfix;
-            }
-          }
-          const uint32_t ci = colp(i) + SZ * gl, cj = colp(j) + SZ * gl;
-          T x[E], y[E];
-          T g = T(0);
+              const T al = active ? nrm2[i] : T(0), be = active ? nrm2[j] : T(0);
+              if (al > T(0) && be > T(0) && g * g > tol2 * al * be) {
+                T cs, sn, t;
+                rotation_fast(al, be, g, cs, sn, t);
+                const T hh = sn / (T(1) + cs);
 #pragma unroll
-          for (int e = 0; e < E; ++e) {
-            x[e] = active ? dsm_ld(ci + SZ * G * e, tz) : T(0);
-            y[e] = active ? dsm_ld(cj + SZ * G * e, tz) : T(0);
-          }
-#pragma unroll
-          for (int e = 0; e < E; ++e) g = fma(x[e], y[e], g);
-          g = group_sum<G>(g);
-          if constexpr (kScaled) {
-            // scaled rotations in three phases, as in jacobi_svt_kernel
-            if (gl == 0) s_pg[grp] = g;
-            __syncthreads();
-            const int batch = min(ngrp, mine - k0);
-            for (int q = threadIdx.x; q < batch; q += blockDim.x) {
-              const int kq = (k0 + q) * C + rank;
-              int pi, pj;
-              if (kq == 0) {
-                pi = cfix;
-                pj = rnd;
-              } else {
-                pi = rnd + kq;
-                if (pi >= cfix) pi -= cfix;
-                pj = rnd - kq;
-                if (pj < 0) pj += cfix;
-              }
-              const uint32_t npi = nrmp(pi), npj = nrmp(pj), dpi = dscp(pi), dpj = dscp(pj);
-              const uint32_t ipi = iscp(pi), ipj = iscp(pj);
-              const T al = dsm_ld(npi, tz), be = dsm_ld(npj, tz);
-              const T di = dsm_ld(dpi, tz), dj = dsm_ld(dpj, tz);
-              const T ei = dsm_ld(ipi, tz), ej = dsm_ld(ipj, tz);
-              const T gq = s_pg[q] * (di * dj);
-              int rot = 0;
-              if (al > T(0) && be > T(0) && gq * gq > tol2 * al * be) {
-                T cs, ic, t;
-                rotation_scaled(al, be, gq, cs, ic, t);
-                T di2 = di * cs, dj2 = dj * cs, ei2 = ei * ic, ej2 = ej * ic;
-                s_pa[q] = t * dj * ei;
-                s_pb[q] = t * di * ej;
-                T fx = T(1), fy = T(1);
-                if (di2 < T(0x1p-64)) { fx = di2; di2 = ei2 = T(1); }
-                if (dj2 < T(0x1p-64)) { fy = dj2; dj2 = ej2 = T(1); }
-                s_sx[q] = fx;
-                s_sy[q] = fy;
-                dsm_st(npi, al - t * gq);
-                dsm_st(npj, be + t * gq);
-                dsm_st(dpi, di2);
-                dsm_st(dpj, dj2);
-                dsm_st(ipi, ei2);
-                dsm_st(ipj, ej2);
-                ++nrot;
+                for (int e = 0; e < E; ++e) {
+                  ci[gl + G * e] = fma(-sn, fma(hh, x[e], y[e]), x[e]);
+                  cj[gl + G * e] = fma(sn, fma(-hh, y[e], x[e]), y[e]);
+                }
+                if (gl == 0) {
+                  nrm2[i] = al - t * g;
+                  nrm2[j] = be + t * g;
+                  ++nrot;
+                }
                 flag = 1;
-                rot = 1;
-              }
-              s_pr[q] = rot;
-            }
-            __syncthreads();
-            if (active && s_pr[grp]) {
-              const T alpha = s_pa[grp], beta = s_pb[grp];
-#pragma unroll
-              for (int e = 0; e < E; ++e) {
-                const T xe = x[e], ye = y[e];
-                x[e] = fma(-alpha, ye, xe);
-                y[e] = fma(beta, xe, ye);
-              }
-              const T fx = s_sx[grp], fy = s_sy[grp];
-              if (fx != T(1)) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) x[e] *= fx;
-              }
-              if (fy != T(1)) {
-#pragma unroll
-                for (int e = 0; e < E; ++e) y[e] *= fy;
-              }
-#pragma unroll
-              for (int e = 0; e < E; ++e) {
-                dsm_st(ci + SZ * G * e, x[e]);
-                dsm_st(cj + SZ * G * e, y[e]);
               }
             }
-            // the next batch's first barrier orders these reads of s_pa, s_pr before
-            // its writes
-          } else {
-            const uint32_t npi = nrmp(i), npj = nrmp(j);
-            const T al = active ? dsm_ld(npi, tz) : T(0), be = active ? dsm_ld(npj, tz) : T(0);
-            if (al > T(0) && be > T(0) && g * g > tol2 * al * be) {
-              T cs, sn, t;
-              rotation_fast(al, be, g, cs, sn, t);
-              const T h = sn / (T(1) + cs);
+          }
+          __syncthreads();
+        }
+        // move the half-blocks to their holders in the next block round (cyclic, so the
+        // layout at every sweep start is that of block round 0): read the two new
+        // half-blocks (and their scalars) from the current holders in chunks, a cluster
+        // barrier between the reads and the overwrites of each chunk
+        const int nb = (b + 1) % (NB - 1);
+        int srcK[2], srcS[2];
 #pragma unroll
-              for (int e = 0; e < E; ++e) {
-                dsm_st(ci + SZ * G * e, fma(-sn, fma(h, x[e], y[e]), x[e]));
-                dsm_st(cj + SZ * G * e, fma(sn, fma(-h, y[e], x[e]), y[e]));
-              }
-              if (gl == 0) {
-                dsm_st(npi, al - t * g);
-                dsm_st(npj, be + t * g);
-                ++nrot;
-              }
-              flag = 1;
-            }
+        for (int sl = 0; sl < 2; ++sl) {
+          const int x = held(nb, rank, sl);
+          srcK[sl] = 0;
+          srcS[sl] = 0;
+          for (int k = 0; k < C; ++k)
+            for (int s2 = 0; s2 < 2; ++s2)
+              if (held(b, k, s2) == x) { srcK[sl] = k; srcS[sl] = s2; }
+        }
+        const bool keep0 = srcK[0] == rank && srcS[0] == 0;
+        const bool keep1 = srcK[1] == rank && srcS[1] == 1;
+        cl.sync();  // every CTA has finished block round b
+        T s0 = T(0), s1 = T(0), s2v = T(0);
+        const int sq = threadIdx.x;  // scalars: thread sq < 2h moves column sq's three
+        const int ssl = sq / (h > 0 ? h : 1);
+        const bool smove = sq < 2 * h && !(ssl == 0 ? keep0 : keep1);
+        if (smove) {
+          const int src = srcS[ssl] * h + sq % h;
+          s0 = dsm_ld(dsm_addr(nrm2 + src, srcK[ssl]), tz);
+          s1 = dsm_ld(dsm_addr(dsc + src, srcK[ssl]), tz);
+          s2v = dsm_ld(dsm_addr(isc + src, srcK[ssl]), tz);
+        }
+        // chunks are ranges of the offset w inside a half-block, the same for every CTA
+        // and both slots, so that an offset is read (by its next holder) and overwritten
+        // (by its current holder) on opposite sides of the same barrier
+        constexpr int CH = 8;
+        const int per = h * ld, wch = CH * (int)blockDim.x / 2;
+        for (int wb = 0; wb < per; wb += wch) {
+          T buf[CH];
+#pragma unroll
+          for (int u = 0; u < CH; ++u) {
+            const int idx = u * (int)blockDim.x + (int)threadIdx.x;
+            const int sl = idx & 1, w = wb + (idx >> 1);
+            buf[u] = T(0);
+            if (w < per && !(sl == 0 ? keep0 : keep1))
+              buf[u] = dsm_ld(dsm_addr(Wl + (size_t)srcS[sl] * per + w, srcK[sl]), tz);
+          }
+          cl.sync();
+#pragma unroll
+          for (int u = 0; u < CH; ++u) {
+            const int idx = u * (int)blockDim.x + (int)threadIdx.x;
+            const int sl = idx & 1, w = wb + (idx >> 1);
+            if (w < per && !(sl == 0 ? keep0 : keep1)) Wl[(size_t)sl * per + w] = buf[u];
+          }
+          if (wb == 0 && smove) {
+            nrm2[sq] = s0;
+            dsc[sq] = s1;
+            isc[sq] = s2v;
           }
         }
-        cl.sync();
+        __syncthreads();
       }
       flag = __syncthreads_or(flag);
       if (threadIdx.x == 0) dsm_st(dsm_addr(&s_flagslot[sweeps & 1][rank], 0), flag);
@@ -486,16 +543,18 @@ jacobi_svt_cluster_kernel(const JArgs a) {
 
     // ---- 3. shrink and reconstruct: every CTA copies the norms and the permutation of
     // all columns, builds the same list of kept columns, then computes its rows
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    // columns moved between CTAs in the sweeps: scan every padded position (a zero
+    // padding column is never kept); permall indexes the rows of Z (QR order)
+    for (int c = threadIdx.x; c < np; c += blockDim.x) {
       gval[c] = dsm_ld(nrmp(c), tz);
-      permall[c] = dsm_ld(permp(c), 0);
+      if (c < n) permall[c] = dsm_ld(permp(c), 0);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       int st = 0, k = 0;
       T nuc = T(0);
       if (rotated) st |= LT_DEV_NOCONV;
-      for (int c = 0; c < n; ++c) {
+      for (int c = 0; c < np; ++c) {
         const T s2 = gval[c];
         if (!isfinite(s2)) st |= LT_DEV_NONFINITE;
         const T sg = sqrt(s2);

@@ -116,10 +116,10 @@ def test_cluster_pga_vs_oracle(cluster):
 
 def test_cluster_auto_choice():
     """The planner's choice (LT_OPT_JACOBI_CLUSTER = 0) on FP64 144 x 176 slices, bit for
-    bit: 12 slices go to clusters of 4 (48 CTAs instead of 12 on 152 SMs); the 96 of the
-    benchmark stay on single CTAs (clusters of 3 measured no faster there)."""
+    bit: 12 slices go to clusters of 4 (48 CTAs instead of 12 on 152 SMs), the 96 of the
+    benchmark to clusters of 3 (288 CTAs, two per SM)."""
     rng = np.random.default_rng(96)
-    for I4, form in ((4, 4), (32, 1)):
+    for I4, form in ((4, 4), (32, 3)):
         A = rng.standard_normal((144, 176, 3, I4))
         tr = [("dct", 3), ("dct", I4)]
         Da = run_svt(A, 5.0, tr, lt.LT_FP64, 0)
