@@ -376,7 +376,8 @@ def run_ours(args):
         cpu = {"value": args.cpu_iters / dt, "unit": "iters/s", "cores": os.cpu_count(),
                "kind": "oracle",
                "sample": f"{args.cpu_iters} PGA iterations of the same 144x176x3x32 problem "
-                         f"({dt:.1f} s), numpy/LAPACK FP64, BLAS threads = all host cores"}
+                         f"({dt:.1f} s), numpy/LAPACK FP64, BLAS threads = all host cores",
+               "single_thread": oracle_single_thread(obs_np, c, 3)}
 
     if rank == 0:
         peaks = load_peaks()
@@ -432,6 +433,39 @@ def run_ours(args):
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
+
+
+def oracle_single_thread(obs_np, c, iters):
+    """The oracle's PGA on one host thread (BLAS and OpenMP pools set to 1 before numpy
+    loads, in a child process), the setting of the paper's single-core timings: `iters`
+    iterations of the same problem.  Returns {"value", "unit", "cores": 1, "sample"} or
+    {"error": ...}; never raises."""
+    with tempfile.TemporaryDirectory() as td:
+        np.save(os.path.join(td, "obs.npy"), obs_np)
+        np.save(os.path.join(td, "mask.npy"), c["mask"])
+        code = (
+            "import sys, time, json, numpy as np\n"
+            f"sys.path.insert(0, {ROOT!r})\n"
+            "from oracle import lt_oracle as O\n"
+            f"obs = np.load({os.path.join(td, 'obs.npy')!r})\n"
+            f"mask = np.load({os.path.join(td, 'mask.npy')!r})\n"
+            "Ms = [O.dct_matrix(3), O.dct_matrix(32)]\n"
+            "t0 = time.perf_counter()\n"
+            f"O.pga(mask, obs, {c['tau']!r}, {c['step']!r}, {int(iters)}, Ms)\n"
+            "print(json.dumps({'seconds': time.perf_counter() - t0}))\n")
+        env = dict(os.environ)
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                    "BLIS_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+            env[var] = "1"
+        try:
+            r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                               text=True, timeout=300)
+            sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+        except Exception as e:  # the baseline is a report, not part of the product path
+            return {"error": f"{type(e).__name__}: {str(e)[:200]}"}
+    return {"value": round(iters / sec, 4), "unit": "iters/s", "cores": 1,
+            "sample": f"{iters} PGA iterations of the same problem ({sec:.1f} s), BLAS and "
+                      "OpenMP pools of one thread"}
 
 
 def fourier_leg(args, dev, ws, mask_d, obs64, c, flush, cpu):
