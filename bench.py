@@ -49,8 +49,21 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PGA iters/s & L-SVT slices/s, mixed vs FP64 at rel-err<=1e-5; %roofline"
 WORKLOAD = "pga_completion_144x176x3x32_fp64"
-FP64_PEAK_GFLOPS = 1199.4   # measured FP64 FMA throughput of this GB300 pool (probe in DESIGN)
-FP32_PEAK_GFLOPS = 74944.4  # measured FP32 FMA throughput (same probe)
+# FMA throughput of the GPU in GFLOP/s, measured at start-up by lt_measure_fma_peak
+# (eight independent FMA chains per thread, four 512-thread CTAs per SM): the peaks of
+# the ALU-bound rooflines.
+FMA_PEAKS = {}
+PEAK_SOURCE = ("lt_measure_fma_peak on this GPU at start-up (FMA chains, 4 x 512 threads "
+               "per SM, 3 timed launches; of measured)")
+
+
+def fma_peak(name):
+    """Measured FMA peak ("fp64" or "fp32") in GFLOP/s (cached)."""
+    if name not in FMA_PEAKS:
+        from paper_2202_02870_gb300 import lt
+        prec = lt.LT_FP64 if name == "fp64" else lt.LT_FP32
+        FMA_PEAKS[name] = round(max(lt.lt_measure_fma_peak(prec) for _ in range(2)), 1)
+    return FMA_PEAKS[name]
 ORACLE_ITERS_PER_STEP = 3
 
 
@@ -89,12 +102,25 @@ def profiled_traffic(kernel):
     return None
 
 
+# HBM copy bandwidth of the GB300s as the driver measured it at the start of the
+# work (MEASURED_PEAKS.json, hbm_gbs); used when that file is not present on the box.
+HBM_GBS_RECORDED = 6799.6
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f)
     except Exception:
         return {}
+
+
+def hbm_peak():
+    """(GB/s, source) of the HBM roofline."""
+    v = load_peaks().get("hbm_gbs")
+    if v:
+        return float(v), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    return HBM_GBS_RECORDED, "this pool's measured copy bandwidth as recorded (of measured)"
 
 
 def dist_env():
@@ -239,6 +265,8 @@ def run_ours(args):
         return ctx
 
     tune(ctx64, obs64, "fp64")
+    fma_peak("fp64")
+    fma_peak("fp32")
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -316,9 +344,9 @@ def run_ours(args):
                 "transform_ms_per_step": round(tr["ms"] / args.steps, 3),
                 "tc_launches_per_step": stp["tc_launches"] / args.steps,
                 "roofline": {"kernel": "jacobi_svt (FP32)", "bound": "alu",
-                             "achieved": round(jp_ach, 1), "peak": FP32_PEAK_GFLOPS,
-                             "unit": "GFLOP/s", "frac": round(jp_ach / FP32_PEAK_GFLOPS, 4),
-                             "peak_source": "measured FP32 FMA throughput (of measured)"}}
+                             "achieved": round(jp_ach, 1), "peak": fma_peak("fp32"),
+                             "unit": "GFLOP/s", "frac": round(jp_ach / fma_peak("fp32"), 4),
+                             "peak_source": PEAK_SOURCE}}
 
     fp32_leg = single_leg(lt.LT_FP32, "f32")
     mixed_leg = single_leg(lt.LT_MIXED, "f32 + split-tf32x3 tensor cores")
@@ -333,6 +361,11 @@ def run_ours(args):
     batched = None
     if args.batched_steps > 0:
         batched = run_batched_leg(args, dev, ws)
+
+    # ---------------- L-SVT slices/s (config 2 with transforms; config 3's 2048 slices)
+    svt = None
+    if args.svt_steps > 0 and rank == 0:
+        svt = svt_legs(dev, obs64, c, flush, args.svt_steps)
 
     # ---------------- the fifth-order *_L-product (face-wise GEMM on the tensor cores)
     product = None
@@ -380,7 +413,6 @@ def run_ours(args):
                "single_thread": oracle_single_thread(obs_np, c, 3)}
 
     if rank == 0:
-        peaks = load_peaks()
         line = {
             "metric": METRIC,
             "value": round(value, 5),
@@ -404,13 +436,15 @@ def run_ours(args):
             "mixed": mixed_leg,
             "fp32": fp32_leg,
             "autotune": tuned,
+            "fma_peaks_gflops": dict(FMA_PEAKS, source=PEAK_SOURCE),
             "batched": batched,
             "fourier": fourier,
             "product_256x256x16x16x8": product,
+            "svt": svt,
             "roofline": {"kernel": "jacobi_svt (FP64)", "bound": "alu",
-                         "achieved": round(achieved, 2), "peak": FP64_PEAK_GFLOPS,
-                         "unit": "GFLOP/s", "frac": round(achieved / FP64_PEAK_GFLOPS, 4),
-                         "peak_source": "measured FP64 FMA throughput (of measured)",
+                         "achieved": round(achieved, 2), "peak": fma_peak("fp64"),
+                         "unit": "GFLOP/s", "frac": round(achieved / fma_peak("fp64"), 4),
+                         "peak_source": PEAK_SOURCE,
                          "traffic": profiled_traffic("jacobi_svt_fp64"),
                          "flops_per_launch": jac_flops_avg, "ms_per_launch": round(jac_ms_avg, 4)},
             "kernels": {f: {"launches": st64[f]["launches"], "ms": round(st64[f]["ms"], 3),
@@ -418,9 +452,9 @@ def run_ours(args):
                         for f in families},
             "transform_roofline": {
                 "bound": "alu", "achieved": round(tra["flops"] / max(tra["ms"], 1e-9) / 1e6, 2),
-                "unit": "GFLOP/s", "peak": FP64_PEAK_GFLOPS,
+                "unit": "GFLOP/s", "peak": fma_peak("fp64"),
                 "hbm_gbs": round(tra["bytes"] / max(tra["ms"], 1e-9) / 1e6, 1),
-                "hbm_peak_gbs": peaks.get("hbm_gbs")},
+                "hbm_peak_gbs": hbm_peak()[0]},
             "e2e": {"value": round(job_rate(iters, ws, e2e_step), 5), "unit": "iters/s",
                     "ms_per_step": round(e2e_step, 3),
                     "h2d_bytes_per_step": int(N + N * 8), "d2h_bytes_per_step": int(N * 8)},
@@ -509,14 +543,14 @@ def fourier_leg(args, dev, ws, mask_d, obs64, c, flush, cpu):
         step_ms = max_over_ranks(statistics.mean(ms), ws, dev)
         jac = stats["jacobi"]
         gflops = jac["flops"] / max(jac["ms"], 1e-9) / 1e6
-        peak = FP64_PEAK_GFLOPS if prec == lt.LT_FP64 else FP32_PEAK_GFLOPS
+        peak = fma_peak("fp64" if prec == lt.LT_FP64 else "fp32")
         leg = {"value": round(job_rate(iters, ws, step_ms), 4), "unit": "iters/s",
                "ms_per_iter": round(step_ms / iters, 3),
                "jacobi_ms_per_iter": round(jac["ms"] / max(args.fourier_steps * iters, 1), 3),
                "roofline": {"kernel": f"jacobi_svt ({label.upper()})", "bound": "alu",
                             "achieved": round(gflops, 1), "peak": peak, "unit": "GFLOP/s",
                             "frac": round(gflops / peak, 4),
-                            "peak_source": f"measured {label.upper()} FMA throughput (of measured)"},
+                            "peak_source": PEAK_SOURCE},
                "rel_residual": rep.rel_residual, "device_status": rep.device_status}
         if X64 is None:
             X64 = X.double()
@@ -586,6 +620,104 @@ def run_batched_leg(args, dev, ws):
             "speedup_vs_sequential": round(ms_s / ms_b, 3)}
 
 
+def svt_rate(ctx, G, tau, D, wsb, units, steps, warmup, flush):
+    """Per-call time of lt_svt (transforms included) and of its Jacobi launch alone (the
+    library's CUDA events), L2 flushed before every timed call."""
+    import torch
+    from paper_2202_02870_gb300 import lt
+    for _ in range(warmup):
+        lt.lt_svt(ctx, G, tau, D, ws=wsb)
+    torch.cuda.synchronize()
+    lt.lt_ctx_get_stats(ctx, reset=True)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 1)
+    st = torch.cuda.current_stream()
+    ms = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        lt.lt_svt(ctx, G, tau, D, ws=wsb)
+        e1.record(st)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    stats = lt.lt_ctx_get_stats(ctx, reset=True)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 0)
+    jac = stats["jacobi"]
+    jms = jac["ms"] / max(jac["launches"], 1)
+    call = statistics.mean(ms)
+    return {"ms_per_call": round(call, 3), "slices_per_s": round(units / (call / 1e3), 1),
+            "jacobi_ms_per_launch": round(jms, 3),
+            "jacobi_slices_per_s": round(units / (jms / 1e3), 1) if jms > 0 else None,
+            "jacobi_gflops_executed": round(jac["flops"] / max(jac["ms"], 1e-9) / 1e6, 1),
+            "transform_ms_per_call": round(stats["transform"]["ms"] / steps, 3),
+            "tc_launches_per_call": stats["tc_launches"] / steps}
+
+
+def svt_legs(dev, obs64, c, flush, steps):
+    """L-SVT slices/s (Algorithm 4, transforms included, and the Jacobi launch alone):
+    config 2: the 96 transform-domain slices (144 x 176) of G = P_Omega(M), the first
+              PGA iterate's input, tau 0.5, FP64 and FP32;
+    config 3: the 256x256x16x16x8 tensor (U[-1,1], L_k = Q_k diag(d_k), cond 1e2 each),
+              2048 slices of 256 x 256, tau = 0.1 x the median largest singular value
+              of four sampled transform-domain slices, FP64, FP32 and LT_MIXED (its
+              modes 16, 16, 8 are below LT_OPT_TC_MODE_MIN, so it runs the FP32 kernels),
+              with the errors of FP32 / LT_MIXED against the FP64 result."""
+    import torch
+    from paper_2202_02870_gb300 import lt, synth
+    out = {"config2_144x176x3x32": {}, "config3_256x256x16x16x8": {}}
+    mats2 = [lt.lt_make_dct(3), lt.lt_make_dct(32)]
+    for name, prec, dt in (("fp64", lt.LT_FP64, torch.float64), ("fp32", lt.LT_FP32, torch.float32)):
+        ctx = lt.Context([3, 32], mats2, prec)
+        G = obs64.to(dt)
+        D = torch.empty_like(G)
+        wsb = torch.empty(max(lt.lt_workspace_size(ctx, lt.LT_OP_SVT, 144, 176), 1),
+                          dtype=torch.uint8, device=dev)
+        leg = svt_rate(ctx, G, c["tau"], D, wsb, 96, steps, 2, flush)
+        peak = fma_peak(name)
+        leg["jacobi_roofline"] = {"bound": "alu", "achieved": leg["jacobi_gflops_executed"],
+                                  "peak": peak, "unit": "GFLOP/s",
+                                  "frac": round(leg["jacobi_gflops_executed"] / peak, 4),
+                                  "peak_source": PEAK_SOURCE}
+        out["config2_144x176x3x32"][name] = leg
+    c3 = synth.config3()
+    mats3 = [np.asarray(m) for _, m in c3["transforms"]]
+    A64 = torch.from_numpy(np.ascontiguousarray(c3["A"].ravel(order="F"))).reshape(
+        (8, 16, 16, 256, 256)).to(dev)
+    ctx64 = lt.Context([16, 16, 8], mats3, lt.LT_FP64)
+    Ah = torch.empty_like(A64)
+    lt.lt_transform(ctx64, A64, Ah)
+    samples = [0, 513, 1337, 2047]
+    sl = Ah.reshape(2048, 256, 256)[samples]
+    tau3 = 0.1 * float(torch.quantile(torch.linalg.matrix_norm(sl, ord=2), 0.5).item())
+    del Ah, sl
+    D64 = None
+    for name, prec, dt in (("fp64", lt.LT_FP64, torch.float64), ("fp32", lt.LT_FP32, torch.float32),
+                           ("mixed", lt.LT_MIXED, torch.float32)):
+        ctx = ctx64 if prec == lt.LT_FP64 else lt.Context([16, 16, 8], mats3, prec)
+        G = A64.to(dt)
+        D = torch.empty_like(G)
+        wsb = torch.empty(max(lt.lt_workspace_size(ctx, lt.LT_OP_SVT, 256, 256), 1),
+                          dtype=torch.uint8, device=dev)
+        n = 1 if prec == lt.LT_FP64 else max(1, min(steps, 3))
+        leg = svt_rate(ctx, G, tau3, D, wsb, 2048, n, 1, flush)
+        peak = fma_peak("fp64" if prec == lt.LT_FP64 else "fp32")
+        leg["jacobi_roofline"] = {"bound": "alu", "achieved": leg["jacobi_gflops_executed"],
+                                  "peak": peak, "unit": "GFLOP/s",
+                                  "frac": round(leg["jacobi_gflops_executed"] / peak, 4),
+                                  "peak_source": PEAK_SOURCE}
+        leg["device_status"] = lt.lt_last_device_status(ctx)
+        if D64 is None:
+            D64 = D.double()
+        else:
+            leg["rel_err_vs_fp64"] = float(torch.linalg.norm(D.double() - D64) / torch.linalg.norm(D64))
+        out["config3_256x256x16x16x8"][name] = leg
+        del G, D, wsb
+    out["config3_256x256x16x16x8"]["tau"] = tau3
+    del A64, D64
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_case(args):
     """Auxiliary single-operation runs used for profiling (not the benchmark line):
     --case svt     lt_svt (tau 0.5) of the 144x176x3x32 tensor G = P_Omega(M) of the
@@ -644,10 +776,21 @@ def product5_leg(precisions, steps, warmup, tile_n=0):
     from paper_2202_02870_gb300 import lt, synth
     c = synth.config3()
     dev = torch.device("cuda", 0)
-    peaks = load_peaks()
-    hbm = peaks.get("hbm_gbs", 6800.0)
+    hbm, hbm_src = hbm_peak()
     host = {"A": c["A"], "B": c["B"]}
     out = {}
+    # the FP64 GPU product of the same operands: the reference of the other precisions'
+    # errors (the FP64 path itself is pinned to the oracle by the parity tests)
+    C64 = None
+    if any(p in ("fp32", "mixed") for p in precisions):
+        to64 = lambda a: torch.from_numpy(np.ascontiguousarray(a.ravel(order="F"))).reshape(
+            tuple(reversed(a.shape))).to(dev)
+        ctx64 = lt.Context([16, 16, 8], [np.asarray(m) for _, m in c["transforms"]], lt.LT_FP64)
+        A64, B64 = to64(host["A"]), to64(host["B"])
+        C64 = torch.empty((8, 16, 16, 128, 256), dtype=torch.float64, device=dev)
+        lt.lt_product(ctx64, A64, B64, C64)
+        torch.cuda.synchronize()
+        del A64, B64, ctx64
     for name in precisions:
         prec = {"fp64": lt.LT_FP64, "fp32": lt.LT_FP32, "mixed": lt.LT_MIXED}[name]
         dt = torch.float64 if prec == lt.LT_FP64 else torch.float32
@@ -686,20 +829,24 @@ def product5_leg(precisions, steps, warmup, tile_n=0):
                                        for k in ("transform", "gemm", "aux")},
                "tc_launches_per_call": st["tc_launches"] / steps,
                "gemm_roofline": {"bound": "hbm", "achieved": round(gemm_bytes / g_ms / 1e6, 1),
-                                 "peak": hbm, "unit": "GB/s",
+                                 "peak": hbm, "unit": "GB/s", "peak_source": hbm_src,
                                  "frac": round(gemm_bytes / g_ms / 1e6 / hbm, 4),
                                  "algorithmic_bytes": gemm_bytes, "ms_per_launch": round(g_ms, 4),
                                  "tflops_algorithmic": round(gemm_flops / g_ms / 1e9, 2)},
                "transform_roofline": {"bound": "hbm",
                                       "achieved": round(tr["bytes"] / max(tr["ms"], 1e-9) / 1e6, 1),
-                                      "peak": hbm, "unit": "GB/s",
+                                      "peak": hbm, "unit": "GB/s", "peak_source": hbm_src,
                                       "frac": round(tr["bytes"] / max(tr["ms"], 1e-9) / 1e6 / hbm, 4),
                                       "tflops_algorithmic": round(tr["flops"] / max(tr["ms"], 1e-9) / 1e9, 2)}}
         if prec == lt.LT_MIXED:
             leg["gemm_roofline"]["tflops_issued_tf32x3"] = round(3 * gemm_flops / g_ms / 1e9, 2)
+        if C64 is not None and prec != lt.LT_FP64:
+            leg["rel_err_vs_fp64"] = float(torch.linalg.norm(Cd.double() - C64) / torch.linalg.norm(C64))
         out[name] = leg
         del A, B, Cd, ws, ctx
         torch.cuda.empty_cache()
+    del C64
+    torch.cuda.empty_cache()
     return out
 
 
@@ -743,7 +890,6 @@ def run_transform5(args):
         run()
     st = lt.lt_ctx_get_stats(ctx, reset=True)
     tr = st["transform"]
-    peaks = load_peaks()
     print(json.dumps({"case": "transform5", "precision": args.precision,
                       "ms_per_transform_and_inverse": round(ms, 4),
                       "transform_kernel_ms": round(tr["ms"] / args.steps, 4),
@@ -751,7 +897,7 @@ def run_transform5(args):
                       "tc_launches_per_call": st["tc_launches"] / args.steps,
                       "gflops_algorithmic": round(tr["flops"] / max(tr["ms"], 1e-9) / 1e6, 1),
                       "hbm_gbs_algorithmic": round(tr["bytes"] / max(tr["ms"], 1e-9) / 1e6, 1),
-                      "hbm_peak_gbs": peaks.get("hbm_gbs")}))
+                      "hbm_peak_gbs": hbm_peak()[0]}))
 
 
 def run_pga5(args):
@@ -898,6 +1044,8 @@ def main():
                     help="timed steps of the Fourier-operator (TNN-PGA-F) leg; 0 skips it")
     ap.add_argument("--fourier-iters", type=int, default=10,
                     help="PGA iterations per step of the Fourier leg")
+    ap.add_argument("--svt-steps", type=int, default=3,
+                    help="timed calls per precision of the L-SVT legs (0 skips them)")
     ap.add_argument("--product-steps", type=int, default=5,
                     help="timed calls of the fifth-order product leg (0 skips it)")
     ap.add_argument("--i4", type=int, default=40,

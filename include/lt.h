@@ -121,13 +121,24 @@ typedef enum {
                                 step * max(nu^k mu_0, tau).  0 (default) = off, fixed tau.
                                 Not available in lt_pga_complete_batched (LT_ERR_ARG). */
   LT_OPT_NU = 9,             /* PGA continuation decay nu, 0 < nu <= 1 (default 0.9) */
-  LT_OPT_JACOBI_CLUSTER = 10 /* SVT kernel form: 0 = planner's choice (default; FP64:
+  LT_OPT_JACOBI_CLUSTER = 10, /* SVT kernel form: 0 = planner's choice (default; FP64:
                                 a cluster when the launch's slices leave SMs idle or do
                                 not fit one CTA's shared memory, counted as if the launch
                                 had the GPU to itself), 1 = one CTA per slice, 3 or 4 = a
                                 thread-block cluster of that many CTAs per slice (columns
                                 spread over the CTAs' shared memory; slices up to 288
                                 columns after padding) */
+  LT_OPT_TC_WAIT_US = 11,    /* LT_MIXED: limit of every bounded wait inside the
+                                tensor-core kernel, in microseconds (0 = default, 1 s;
+                                at most 60 s).  On expiry the kernel raises
+                                LT_DEV_TIMEOUT, stops issuing work, drains the copies and
+                                products it has in flight, frees its TMEM and returns;
+                                its output is then undefined. */
+  LT_OPT_TC_TEST_NO_LOADS = 12 /* LT_MIXED, for testing the timeout path only: 1 = the
+                                tensor-core kernel's producer issues no copies, so the
+                                other roles' first waits expire after LT_OPT_TC_WAIT_US
+                                and every call that reaches the kernel reports
+                                LT_DEV_TIMEOUT with undefined output; 0 (default) = off */
 } lt_option;
 
 /* Kernel families counted by lt_ctx_get_stats. */
@@ -343,7 +354,12 @@ LT_API lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const in
  * module holds until the process exits.
  * Limits: align256(I1*l*P*elem) + align256(l*I2*P*elem) must not exceed
  *   LT_NOALLOC_SCRATCH_BYTES (align256 rounds up to a multiple of 256), else
- *   LT_ERR_SHAPE and nothing is enqueued.
+ *   LT_ERR_SHAPE and nothing is enqueued (the sizes are multiplied with overflow
+ *   checks, so no wrapped product passes).
+ * Device: the device current at the call must be the one the context was created on
+ *   (LT_ERR_ARG otherwise).
+ * Counters: these calls add to lt_stats.tc_launches (their tensor-core launches) but
+ *   to no other counter of lt_ctx_get_stats, and LT_OPT_PROFILE does not time them.
  * Set-up: the first call made while a device is current looks up the array's device
  *   address on that device (cudaGetSymbolAddress); make that first call before any
  *   stream capture.
@@ -384,6 +400,15 @@ LT_API lt_status lt_autotune_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void*
 LT_API lt_status lt_autotune_product(lt_ctx ctx, int64_t I1, int64_t l, int64_t I2, const void* A,
                                      const void* B, void* C, void* ws, size_t ws_bytes,
                                      void* stream, lt_tune_report* report);
+
+/* Measurement utility (the paper has no counterpart): the FMA throughput of the current
+ * GPU for LT_FP64 or LT_FP32, in GFLOP/s (an FMA = 2 flops), measured by a kernel of
+ * eight independent multiply-add chains per thread on four 512-thread CTAs per SM, one
+ * warm-up and three timed launches on `stream`.  It is the peak against which the ALU
+ * rooflines of the Jacobi and transform kernels are stated.  Synchronises `stream`;
+ * takes about 0.1 s.  gflops: host.  Errors: LT_ERR_ARG (other precisions, NULL),
+ * LT_ERR_CUDA. */
+LT_API lt_status lt_measure_fma_peak(lt_precision prec, double* gflops, void* stream);
 
 /* Counters of the context since creation or the last reset (reset != 0 clears them
  * after reading).  Synchronises the device when LT_OPT_PROFILE is on or when Jacobi

@@ -505,6 +505,14 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
       if (!(value > 0.0 && value <= 1.0)) return LT_ERR_ARG;
       c->nu = value;
       return LT_OK;
+    case LT_OPT_TC_WAIT_US:
+      if (!(value >= 0.0 && value <= 60e6)) return LT_ERR_ARG;
+      c->tc_wait_us = value;
+      return LT_OK;
+    case LT_OPT_TC_TEST_NO_LOADS:
+      if (!(value == 0 || value == 1)) return LT_ERR_ARG;
+      c->tc_no_loads = (int)value;
+      return LT_OK;
     case LT_OPT_TC_TILE_N:
       if (!(value == 0 || value == 32 || value == 64 || value == 128 || value == 256))
         return LT_ERR_ARG;

@@ -106,6 +106,7 @@ cudaError_t launch_facewise_gemm(const Ctx& c, int64_t M, int64_t N, int64_t Kd,
     g.A = static_cast<const float*>(A); g.lda = M; g.sA = M * Kd;
     g.B = static_cast<const float*>(B); g.ldb = Kd; g.sB = Kd * N;
     g.D = static_cast<float*>(C); g.ldd = M; g.sD = M * N;
+    g.wait_ns = (uint64_t)(c.tc_wait_us * 1e3); g.no_loads = c.tc_no_loads;
     if (tc_gemm_supported(g, c.tc_tile_n)) {
       ++c.tc_launches;
       return launch_tc_gemm(g, c.tc_tile_n, c.d_status, st);

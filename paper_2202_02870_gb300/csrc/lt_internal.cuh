@@ -42,6 +42,8 @@ struct Ctx {
   int tc_mode_min = 64;               // LT_MIXED: modes of at least this size (and not
                                       // mode 3) run as tensor-core passes; 0 = never
   int tc_tile_n = 0;                  // LT_MIXED: forced tensor-core tile width (0 = auto)
+  double tc_wait_us = 0.0;            // LT_MIXED: tensor-core wait limit (0 = default 1 s)
+  int tc_no_loads = 0;                // LT_MIXED test switch: no TMA copies are issued
   double mu0 = 0.0;                   // PGA continuation: mu_0 (0 = off)
   double nu = 0.9;                    // PGA continuation: decay of mu
   mutable int64_t tc_launches = 0;    // tensor-core kernel launches (lt_ctx_get_stats)
@@ -151,6 +153,8 @@ struct TcGemm {
   int64_t ldb = 0, sB = 0;
   float* D = nullptr;
   int64_t ldd = 0, sD = 0;
+  uint64_t wait_ns = 0;    // limit of the kernel's bounded waits (0: the default, 1 s)
+  int no_loads = 0;        // test switch: no copies are issued, the waits expire
 };
 
 int tc_tile_n(const TcGemm& g, int forced);

@@ -32,6 +32,20 @@ void* g_addr[kMaxDevices] = {};
 
 size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Bytes of one transform-domain operand (rows x cols x P elements of elem bytes) rounded
+// up to 256, in *out; false when the product overflows or the operand alone exceeds the
+// array (so that no wrapped size can pass the limit check).
+bool operand_bytes(int64_t rows, int64_t cols, int64_t P, int elem, size_t* out) {
+  size_t b = 0;
+  if (rows < 0 || cols < 0 || P < 0 || elem < 0) return false;
+  if (__builtin_mul_overflow((size_t)rows, (size_t)cols, &b) ||
+      __builtin_mul_overflow(b, (size_t)P, &b) || __builtin_mul_overflow(b, (size_t)elem, &b))
+    return false;
+  if (b > (size_t)LT_NOALLOC_SCRATCH_BYTES) return false;
+  *out = align256(b);
+  return *out <= (size_t)LT_NOALLOC_SCRATCH_BYTES;
+}
+
 // Device address of g_noalloc_scratch on the current device (looked up once).
 lt_status scratch_address(void** out) {
   int dev = -1;
@@ -56,9 +70,14 @@ extern "C" lt_status lt_product_noalloc(lt_ctx ctx, int64_t I1, int64_t l, int64
   if (I1 < 1 || l < 1 || I2 < 1) return LT_ERR_ARG;
   if (I1 > (1 << 20) || l > (1 << 20) || I2 > (1 << 20)) return LT_ERR_SHAPE;
   const lt::Ctx& c = *reinterpret_cast<lt::Ctx*>(ctx);
-  const size_t a_bytes = align256((size_t)I1 * l * c.P * c.elem);
-  const size_t b_bytes = align256((size_t)l * I2 * c.P * c.elem);
-  if (a_bytes + b_bytes > (size_t)LT_NOALLOC_SCRATCH_BYTES) return LT_ERR_SHAPE;
+  // The kernels run on the current device; the context's matrices live on c.device.
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return LT_ERR_CUDA;
+  if (dev != c.device) return LT_ERR_ARG;
+  size_t a_bytes = 0, b_bytes = 0;
+  if (!operand_bytes(I1, l, c.P, c.elem, &a_bytes) || !operand_bytes(l, I2, c.P, c.elem, &b_bytes) ||
+      a_bytes > (size_t)LT_NOALLOC_SCRATCH_BYTES - b_bytes)
+    return LT_ERR_SHAPE;
   lt::TransformPlan pa, pb, pc;
   lt_status s;
   if ((s = lt::plan_transform(c, I1 * l, false, &pa)) != LT_OK) return s;

@@ -1,10 +1,13 @@
 // Kernel G on the fifth-generation tensor cores (LT_MIXED contexts): the batched product
 //   D_b = A_b B_b,  b = 0 .. batch-1,
 // in split TF32.  Every FP32 operand x is split as x = hi + lo with hi = tf32(x) and
-// lo = tf32(x - hi), and the tile accumulates hi_A hi_B + hi_A lo_B + lo_A hi_B in FP32
-// (the three-term product: the dropped lo_A lo_B term and the rounding of lo are below
-// 2^-21 |a b| per product, so the result carries about 21 significant bits plus FP32
-// accumulation error).
+// lo = tf32(x - hi), and the tile accumulates hi_A hi_B in one FP32 accumulator and
+// hi_A lo_B + lo_A hi_B in a second one, added in the epilogue (the three-term product:
+// the dropped lo_A lo_B term and the rounding of lo are below 2^-21 |a b| per product).
+// The tensor cores' FP32 accumulation rounds toward zero: measured on the mode
+// products (K = 32 .. 120) with one accumulator for all three terms, the relative error
+// was a bias of -2.5e-7 .. -7.8e-7, growing with K; keeping the small terms apart leaves
+// the large accumulator a third of the additions.
 //
 // It serves the two dense contractions of the method:
 //  * the face-wise product of Sec. 3.1 inside Algorithm 2: A_b = L(A)^p (I1 x l),
@@ -28,17 +31,18 @@
 //             registers and release it at once, then write hi and lo of A transposed
 //             into the K-major 128-byte-swizzled layout and hi and lo of B at the raw
 //             (swizzled) positions into a ring of two converted stages.
-//   warp 13   TMEM allocation (two accumulators of BN columns) and the MMA issuer (one
-//             thread): per 8-deep K step three tcgen05.mma kind::tf32 (hi hi, hi lo,
-//             lo hi) into the 128 x BN FP32 accumulator of the tile; tcgen05.commit
-//             releases a converted stage and, after the last chunk, hands the
-//             accumulator to the epilogue.
-//   warps 0-3 epilogue: TMEM -> registers (tcgen05.ld, one row per thread) -> global
-//             (32 consecutive rows per warp store) while the next tile accumulates in
-//             the other accumulator.
-// Every wait on an mbarrier is bounded (1 s): on expiry the CTA raises LT_DEV_TIMEOUT,
-// every role stops issuing work, the producer waits (bounded) for its copies in flight,
-// the issuer for its MMAs, the TMEM is freed and the CTA returns.
+//   warp 13   TMEM allocation (two stages of two 128 x BN accumulators; one stage when
+//             BN = 256) and the MMA issuer (one thread): per 8-deep K step three
+//             tcgen05.mma kind::tf32, hi hi into the stage's first accumulator, hi lo and
+//             lo hi into its second; tcgen05.commit releases a converted stage and, after
+//             the last chunk, hands the accumulator stage to the epilogue.
+//   warps 0-3 epilogue: TMEM -> registers (tcgen05.ld of both accumulators, one row per
+//             thread), their sum -> global (32 consecutive rows per warp store) while
+//             the next tile accumulates in the other stage.
+// Every wait on an mbarrier is bounded (1 s by default, TcGemm::wait_ns): on expiry the
+// CTA raises LT_DEV_TIMEOUT, every role stops issuing work, the producer waits (bounded)
+// for its copies in flight, the issuer for its MMAs, the TMEM is freed and the CTA
+// returns.
 #include <cuda.h>
 
 #include <mutex>
@@ -56,7 +60,7 @@ constexpr int kConv = 256;                    // converter threads
 constexpr int kMaxRaw = 6;                    // raw (TMA) stages at most
 constexpr uint32_t kABytes = kBM * kBK * 4;   // 16 KiB per A buffer
 constexpr int kSmemLimit = 232448;            // opt-in shared memory per block
-constexpr unsigned long long kWaitNs = 1000000000ull;
+constexpr unsigned long long kWaitNs = 1000000000ull;  // default wait limit (1 s)
 
 struct TcParams {
   int64_t M, N, K, batch;
@@ -67,6 +71,9 @@ struct TcParams {
   int conv_stages;      // converted-operand ring depth (1 or 2)
   int b_batched;        // B has a batch coordinate (else every block uses B_0)
   int32_t* status;      // device status word (LT_DEV_TIMEOUT)
+  unsigned long long wait_ns;  // limit of every mbarrier wait
+  int no_loads;         // test switch: the producer issues no copies, so the first
+                        // waits of the other roles expire (LT_DEV_TIMEOUT)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -105,17 +112,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Waits for the completion of the mbarrier phase of the given parity.  Gives up after
-// kWaitNs (raising the CTA's abort flag and LT_DEV_TIMEOUT) or, when honour_abort is
+// wait_ns (raising the CTA's abort flag and LT_DEV_TIMEOUT) or, when honour_abort is
 // set, as soon as another role of the CTA has given up.
 __device__ bool mbar_wait(uint32_t a, uint32_t parity, volatile int* abort_flag,
-                          int32_t* status, bool honour_abort) {
+                          int32_t* status, bool honour_abort, unsigned long long wait_ns) {
   if (mbar_try(a, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try(a, parity)) return true;
     if ((i & 127u) == 0) {
       if (honour_abort && *abort_flag) return false;
-      if (global_ns() - t0 > kWaitNs) {
+      if (global_ns() - t0 > wait_ns) {
         *abort_flag = 1;
         atomicOr(status, LT_DEV_TIMEOUT);
         return false;
@@ -204,8 +211,12 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
   constexpr uint32_t kBBytes = BN * 128;                  // one B buffer: BN rows of 128 B
   constexpr uint32_t kRawBytes = kABytes + kBBytes;       // raw A [k][m] + raw B (swizzled)
   constexpr uint32_t kConvBytes = 2 * kABytes + 2 * kBBytes;  // A hi, A lo, B hi, B lo
+  // An accumulator stage is a pair of 128 x BN FP32 accumulators: hi hi in the first,
+  // hi lo + lo hi in the second (added in the epilogue).  Two stages (the epilogue of a
+  // tile overlaps the products of the next) where they fit the 512 TMEM columns.
   constexpr uint32_t kAccCols = BN < 32 ? 32 : BN;
-  constexpr uint32_t kTmemCols = 2 * kAccCols;            // two accumulators
+  constexpr int kStages = 4 * kAccCols <= 512 ? 2 : 1;
+  constexpr uint32_t kTmemCols = kStages * 2 * kAccCols;  // a power of two, 128..512
   extern __shared__ unsigned char smem_raw[];
   const uint32_t raw_addr = smem_u32(smem_raw);
   const uint32_t base = (raw_addr + 1023u) & ~1023u;      // swizzled tiles: 1024-aligned
@@ -275,7 +286,7 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
       int last[kMaxRaw];
       for (int i = 0; i < kMaxRaw; ++i) last[i] = -1;
       int64_t g = 0;
-      bool ok = true;
+      bool ok = !p.no_loads;
       for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x) {
         int64_t b;
         int m0, n0;
@@ -283,7 +294,7 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
         for (int c = 0; c < nchunks; ++c, ++g) {
           const int r = (int)(g % R);
           if (g >= R && !mbar_wait(raw_empty(r), (uint32_t)((g / R) - 1) & 1u, abort_flag,
-                                   p.status, true)) {
+                                   p.status, true, p.wait_ns)) {
             ok = false;
             break;
           }
@@ -296,7 +307,7 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
       }
       // never leave while copies into this CTA's shared memory are in flight
       for (int i = 0; i < R; ++i)
-        if (last[i] >= 0) mbar_wait(raw_full(i), (uint32_t)last[i] & 1u, abort_flag, p.status, false);
+        if (last[i] >= 0) mbar_wait(raw_full(i), (uint32_t)last[i] & 1u, abort_flag, p.status, false, p.wait_ns);
     }
   } else if (warp == 13) {
     // ---------------------------------------------------------------- MMA issuer
@@ -308,15 +319,16 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
       int64_t g = 0, it = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; ok && t < ntiles; t += gridDim.x, ++it) {
-        const int a = (int)(it & 1);
-        if (it >= 2 && !mbar_wait(acc_empty(a), (uint32_t)((it / 2) - 1) & 1u, abort_flag,
-                                  p.status, true))
+        const int a = (int)(it % kStages);
+        if (it >= kStages && !mbar_wait(acc_empty(a), (uint32_t)((it / kStages) - 1) & 1u, abort_flag,
+                                  p.status, true, p.wait_ns))
           break;
         tc_fence_after();
-        const uint32_t dacc = tmem + (uint32_t)a * kAccCols;
+        const uint32_t dmain = tmem + (uint32_t)a * 2 * kAccCols;  // hi hi
+        const uint32_t dsmall = dmain + kAccCols;                   // hi lo + lo hi
         for (int c = 0; c < nchunks; ++c, ++g) {
           const int q = (int)(g % C);
-          if (!mbar_wait(conv_full(q), (uint32_t)(g / C) & 1u, abort_flag, p.status, true)) {
+          if (!mbar_wait(conv_full(q), (uint32_t)(g / C) & 1u, abort_flag, p.status, true, p.wait_ns)) {
             ok = false;
             break;
           }
@@ -327,17 +339,17 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
 #pragma unroll
           for (int ks = 0; ks < kBK / 8; ++ks) {  // 8 TF32 = 32 bytes per MMA
             const uint32_t off = 32u * ks;
-            mma_tf32(dacc, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc,
-                     (c > 0 || ks > 0) ? 1u : 0u);
-            mma_tf32(dacc, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
-            mma_tf32(dacc, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+            const uint32_t acc = (c > 0 || ks > 0) ? 1u : 0u;
+            mma_tf32(dmain, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, acc);
+            mma_tf32(dsmall, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, acc);
+            mma_tf32(dsmall, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
           }
           mma_commit(conv_empty(q));
         }
         if (ok) mma_commit(acc_full(a));
       }
       mma_commit(done_bar);  // completes once every MMA issued above has finished
-      mbar_wait(done_bar, 0u, abort_flag, p.status, false);
+      mbar_wait(done_bar, 0u, abort_flag, p.status, false, p.wait_ns);
     }
   } else if (warp >= 4) {
     // ---------------------------------------------------------------- converters
@@ -352,7 +364,7 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
     for (int64_t tt = blockIdx.x; ok && tt < ntiles; tt += gridDim.x) {
       for (int c = 0; c < nchunks; ++c, ++g) {
         const int r = (int)(g % R), q = (int)(g % C);
-        if (!mbar_wait(raw_full(r), (uint32_t)(g / R) & 1u, abort_flag, p.status, true)) {
+        if (!mbar_wait(raw_full(r), (uint32_t)(g / R) & 1u, abort_flag, p.status, true, p.wait_ns)) {
           ok = false;
           break;
         }
@@ -367,7 +379,7 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
         for (int i = 0; i < kBVec; ++i) bv[i] = braw[t + kConv * i];
         mbar_arrive(raw_empty(r));  // the raw stage may be refilled
         if (g >= C && !mbar_wait(conv_empty(q), (uint32_t)((g / C) - 1) & 1u, abort_flag,
-                                 p.status, true)) {
+                                 p.status, true, p.wait_ns)) {
           ok = false;
           break;
         }
@@ -406,8 +418,9 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
     // ---------------------------------------------------------------- epilogue (warps 0-3)
     int64_t it = 0;
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x, ++it) {
-      const int a = (int)(it & 1);
-      bool ok = mbar_wait(acc_full(a), (uint32_t)(it / 2) & 1u, abort_flag, p.status, true);
+      const int a = (int)(it % kStages);
+      bool ok = mbar_wait(acc_full(a), (uint32_t)(it / kStages) & 1u, abort_flag, p.status, true,
+                          p.wait_ns);
       if (!__all_sync(0xffffffffu, ok)) break;  // warp-uniform for tcgen05.ld
       tc_fence_after();
       int64_t b;
@@ -415,17 +428,19 @@ tc_gemm_tf32x3(const __grid_constant__ CUtensorMap map_a,
       tile_coords(t, b, m0, n0);
       const int64_t m = (int64_t)m0 + warp * 32 + lane;
       float* Dp = p.D + b * p.sD;
-      const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)a * kAccCols;
+      const uint32_t lane_addr =
+          tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)a * 2 * kAccCols;
 #pragma unroll 1
       for (int cc = 0; cc < BN; cc += 16) {
         if (n0 + cc >= p.N) break;  // uniform across the warp
-        uint32_t acc[16];
+        uint32_t acc[16], sml[16];
         tmem_ld16(lane_addr + (uint32_t)cc, acc);
+        tmem_ld16(lane_addr + kAccCols + (uint32_t)cc, sml);
         if (m < p.M) {
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const int64_t n = (int64_t)n0 + cc + j;
-            if (n < p.N) Dp[m + n * p.ldd] = __uint_as_float(acc[j]);
+            if (n < p.N) Dp[m + n * p.ldd] = __uint_as_float(acc[j]) + __uint_as_float(sml[j]);
           }
         }
       }
@@ -500,6 +515,7 @@ int smem_for(int raw, int conv) { return raw * raw_bytes<BN>() + conv * conv_byt
 template <int BN>
 cudaError_t launch_bn(const TcGemm& g, const CUtensorMap& ma, const CUtensorMap& mb,
                       int32_t* status, cudaStream_t st) {
+  static_assert(sizeof(unsigned long long) == sizeof(uint64_t), "wait limit width");
   TcParams p;
   p.M = g.M; p.N = g.N; p.K = g.K; p.batch = g.batch;
   p.D = g.D; p.ldd = g.ldd; p.sD = g.sD;
@@ -508,6 +524,8 @@ cudaError_t launch_bn(const TcGemm& g, const CUtensorMap& ma, const CUtensorMap&
   ring_for<BN>(&p.raw_stages, &p.conv_stages);
   p.b_batched = g.sB != 0 ? 1 : 0;
   p.status = status;
+  p.wait_ns = g.wait_ns > 0 ? (unsigned long long)g.wait_ns : kWaitNs;
+  p.no_loads = g.no_loads ? 1 : 0;
   const int64_t tiles = g.batch * p.m_tiles * p.n_tiles;
   if (tiles < 1 || p.raw_stages < 1) return cudaErrorInvalidValue;
   int dev = 0, sms = 0;

@@ -549,6 +549,7 @@ cudaError_t launch_transform(const Ctx& c, const TransformPlan& plan, const void
       g.A = static_cast<const float*>(a.in); g.lda = a.p.Sg; g.sA = a.p.Sg * I;
       g.B = (plan.inverse ? c.d_tc_inv : c.d_tc_fwd) + c.tc_off[q]; g.ldb = c.tc_ld[q]; g.sB = 0;
       g.D = static_cast<float*>(out); g.ldd = a.p.Sg; g.sD = a.p.Sg * I;
+      g.wait_ns = (uint64_t)(c.tc_wait_us * 1e3); g.no_loads = c.tc_no_loads;
       if (tc_gemm_supported(g, c.tc_tile_n)) {
         const cudaError_t e = launch_tc_gemm(g, c.tc_tile_n, c.d_status, st);
         if (e != cudaSuccess) return e;

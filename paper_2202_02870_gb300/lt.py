@@ -29,7 +29,7 @@ LT_FP64, LT_FP32, LT_MIXED = 0, 1, 2
  LT_OP_NORMS) = range(8)
 (LT_OPT_MAX_SWEEPS, LT_OPT_JACOBI_TOL, LT_OPT_OBJECTIVE, LT_OPT_PROFILE, LT_OPT_JACOBI_GROUP,
  LT_OPT_JACOBI_BLOCK, LT_OPT_TC_MODE_MIN, LT_OPT_TC_TILE_N, LT_OPT_MU0, LT_OPT_NU,
- LT_OPT_JACOBI_CLUSTER) = range(11)
+ LT_OPT_JACOBI_CLUSTER, LT_OPT_TC_WAIT_US, LT_OPT_TC_TEST_NO_LOADS) = range(13)
 LT_K_TRANSFORM, LT_K_JACOBI, LT_K_GEMM, LT_K_AUX = 0, 1, 2, 3
 KERNEL_FAMILIES = ("transform", "jacobi", "gemm", "aux")
 
@@ -100,6 +100,7 @@ SIGNATURES = {
     "lt_ctx_get_stats": (C.c_int, [_vp, C.POINTER(lt_stats), C.c_int]),
     "lt_last_device_status": (C.c_int, [_vp, C.POINTER(C.c_int32)]),
     "lt_status_string": (C.c_char_p, [C.c_int]),
+    "lt_measure_fma_peak": (C.c_int, [C.c_int, C.POINTER(C.c_double), _vp]),
 }
 
 _lib: Optional[C.CDLL] = None
@@ -437,3 +438,11 @@ def lt_last_device_status(ctx) -> int:
 
 def lt_status_string(s: int) -> str:
     return lib().lt_status_string(int(s)).decode()
+
+
+def lt_measure_fma_peak(precision: int, stream=None) -> float:
+    """FMA throughput of the current GPU in GFLOP/s (LT_FP64 or LT_FP32)."""
+    out = C.c_double()
+    _check("lt_measure_fma_peak", lib().lt_measure_fma_peak(int(precision), C.byref(out),
+                                                            _stream(stream)))
+    return float(out.value)

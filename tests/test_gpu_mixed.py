@@ -201,3 +201,35 @@ def test_mixed_options_reject_bad_values():
                      (lt.LT_OPT_TC_MODE_MIN, -1), (lt.LT_OPT_TC_MODE_MIN, 2.5)):
         with pytest.raises(lt.LtError):
             lt.lt_ctx_set_option(ctx, opt, bad)
+    for opt, bad in ((lt.LT_OPT_TC_WAIT_US, -1.0), (lt.LT_OPT_TC_WAIT_US, 1e9),
+                     (lt.LT_OPT_TC_TEST_NO_LOADS, 2)):
+        with pytest.raises(lt.LtError):
+            lt.lt_ctx_set_option(ctx, opt, bad)
+
+
+def test_tc_bounded_wait_expires_then_context_recovers():
+    """Failure detection of the tensor-core kernel without a GPU fault: with the test
+    switch LT_OPT_TC_TEST_NO_LOADS the producer issues no copies, so the converters' and
+    the issuer's first waits (limit 5 ms) expire and every role returns (no copy or MMA
+    in flight, TMEM freed).  The call reports LT_DEV_TIMEOUT through the device status
+    word; with the switch off the same context then computes the product correctly."""
+    rng = np.random.default_rng(515)
+    A = rng.uniform(-1, 1, (128, 32, 3))
+    B = rng.uniform(-1, 1, (32, 64, 3))
+    tr = [("dct", 3)]
+    ctx = make_ctx(tr, MIXED)
+    Ad, Bd = to_dev(A, torch.float32), to_dev(B, torch.float32)
+    Cd = empty_dev((128, 64, 3), torch.float32)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_WAIT_US, 5000)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_TEST_NO_LOADS, 1)
+    lt.lt_product(ctx, Ad, Bd, Cd)
+    torch.cuda.synchronize()
+    assert lt.lt_last_device_status(ctx) & lt.LT_DEV_TIMEOUT
+    assert tc_launches(ctx) == 1
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_TEST_NO_LOADS, 0)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_WAIT_US, 0)
+    lt.lt_product(ctx, Ad, Bd, Cd)
+    torch.cuda.synchronize()
+    assert lt.lt_last_device_status(ctx) == 0
+    assert tc_launches(ctx) == 1
+    assert rel(from_dev(Cd, (128, 64, 3)), O.product(A, B, oracle_mats(tr))) <= TOL

@@ -152,18 +152,24 @@ def test_svd_invariants(prec, shape, transforms):
     torch.cuda.synchronize()
     Uh, Sh, Vh = (from_dev(t, s) for t, s in ((U, (I1, I1) + trailing), (S, (I1, I2) + trailing),
                                                 (V, (I2, I2) + trailing)))
-    tol = TOL[prec] * 100
+    tol = TOL[prec]
     rec = O.product(O.product(Uh, Sh, Ms), O.transpose(Vh, Ms), Ms)
-    assert rel(rec, A) <= tol
+    e_rec = rel(rec, A)
     _, _, _, sig_ref = O.svd(A, Ms)
-    assert rel(sig.double().cpu().numpy().T, sig_ref) <= tol
+    e_sig = rel(sig.double().cpu().numpy().T, sig_ref)
     Lu, Ls, Lv = (O.slices(O.transform(T, Ms)) for T in (Uh, Sh, Vh))
+    e_u = max(np.abs(Lu[:, :, p].T @ Lu[:, :, p] - np.eye(I1)).max() for p in range(P))
+    e_v = max(np.abs(Lv[:, :, p].T @ Lv[:, :, p] - np.eye(I2)).max() for p in range(P))
+    e_off = 0.0
     for p in range(P):
-        assert np.abs(Lu[:, :, p].T @ Lu[:, :, p] - np.eye(I1)).max() <= tol * 10
-        assert np.abs(Lv[:, :, p].T @ Lv[:, :, p] - np.eye(I2)).max() <= tol * 10
         off = Ls[:, :, p].copy()
         np.fill_diagonal(off, 0)
-        assert np.abs(off).max() <= tol * np.abs(Ls).max()
+        e_off = max(e_off, np.abs(off).max() / np.abs(Ls).max())
+    print(f"svd invariants prec {prec} {shape}: reconstruction {e_rec:.2e}, sigma {e_sig:.2e}, "
+          f"L(U) orth {e_u:.2e}, L(V) orth {e_v:.2e}, L(S) off-diagonal {e_off:.2e}")
+    assert e_rec <= tol and e_sig <= tol
+    assert e_u <= tol and e_v <= tol
+    assert e_off <= tol
 
 
 # ------------------------------------------------------------------ SVT
@@ -301,7 +307,39 @@ def test_pga_small(prec):
     ref, info = O.pga(c["mask"], obs, 0.3, 1.0, 25, Ms)
     assert rep.iters_done == 25
     assert rel(from_dev(X, obs.shape), ref) <= TOL[prec]
-    assert abs(rep.rel_residual - info["residual"][-1]) <= 1e-8 + TOL[prec] * 10
+    # r = ||Y - X^{k+1}|| / ||X^{k+1}|| with Y = X^k + beta (X^k - X^{k-1}), beta < 1:
+    # relative errors e of the iterates (e <= TOL) move r by at most (3 + 1 + r) e
+    dr = abs(rep.rel_residual - info["residual"][-1])
+    print(f"pga small prec {prec}: residual {info['residual'][-1]:.6e}, |dr| {dr:.2e}")
+    assert dr <= (4.0 + info["residual"][-1]) * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_pga_objective(prec):
+    """The objective of the last iterate, F = tau sum_p ||L(X^{k+1})^p||_* +
+    1/2 ||P_Omega(X^{k+1} - M)||^2 (Theorem 21 / Eq. 24 with orthonormal L, the g + f of
+    Sec. 4), accumulated on the device from the shrunk singular values and the fused
+    inverse transform (LT_OPT_OBJECTIVE), against the oracle's objective, which takes a
+    fresh SVD of every L(X^{k+1})^p.  Checked after 1, 7 and 25 iterations."""
+    c = synth.completion_case(23, 24, 20, (3, 4), rank=3, rho=0.4)
+    c.update(tau=0.3, step=1.0)
+    Xt, obs, Ms = completion_inputs(c)
+    dt = dtype_of(prec)
+    for iters in (1, 7, 25):
+        ctx = make_ctx(c["transforms"], prec)
+        lt.lt_ctx_set_option(ctx, lt.LT_OPT_OBJECTIVE, 1)
+        X = to_dev(np.zeros(obs.shape), dt)
+        rep = lt.lt_pga_report()
+        lt.lt_pga_complete(ctx, to_dev(c["mask"]), to_dev(obs, dt), c["tau"], c["step"], iters,
+                           X, report=rep)
+        torch.cuda.synchronize()
+        _, info = O.pga(c["mask"], obs, c["tau"], c["step"], iters, Ms, objective=True)
+        ref = info["objective"][-1]
+        err = abs(rep.objective - ref) / abs(ref)
+        print(f"pga objective prec {prec} iters {iters}: {rep.objective:.15e} vs "
+              f"{ref:.15e}, rel {err:.2e}")
+        assert rep.iters_done == iters and rep.device_status == 0
+        assert err <= TOL[prec], (iters, err)
 
 
 def test_pga_step_and_tolerance_stop():
@@ -526,17 +564,20 @@ def test_pga_batched_config4_full(prec):
     """The 64-problem batch of uneven sizes (I1 x I2 from 64 x 48 to 512 x 384, I3 = 3,
     I4 in {8, 16, 32, 64}), FP32 and LT_MIXED (the benchmark's batched leg; its I4 = 64
     problems put the mode-4 products on the tensor cores): every problem completes its
-    iterations without device errors, and two of them (for LT_MIXED one with I4 = 64)
-    equal their single-problem runs bit for bit."""
+    iterations without device errors, two of them (for LT_MIXED one with I4 = 64) equal
+    their single-problem runs bit for bit, and the largest problem (512 x 384 x 3 x 16)
+    and the first with I4 = 64 (320 x 240 x 3 x 64) match the FP64 oracle within 1e-5."""
     shapes = synth.config4_shapes()
     rng = np.random.default_rng(4)
-    ctxs, masks, obss, Xs = [], [], [], []
+    ctxs, masks, obss, Xs, host = [], [], [], [], []
     for i, sh in enumerate(shapes):
         full = (sh["I1"], sh["I2"]) + sh["trailing"]
         ctxs.append(make_ctx([("dct", n) for n in sh["trailing"]], prec))
         m = (rng.random(full) < sh["rho"]).astype(np.uint8)
+        o = m * rng.standard_normal(full)
+        host.append((m, o.astype(np.float32).astype(np.float64)))
         masks.append(to_dev(m))
-        obss.append(to_dev(m * rng.standard_normal(full), torch.float32))
+        obss.append(to_dev(o, torch.float32))
         Xs.append(torch.zeros(tuple(reversed(full)), dtype=torch.float32, device="cuda"))
     reps = []
     lt.lt_pga_complete_batched(ctxs, masks, obss, [0.5] * 64, [1.0] * 64, 4, Xs, reports=reps)
@@ -551,3 +592,13 @@ def test_pga_batched_config4_full(prec):
         lt.lt_pga_complete(ctxs[i], masks[i], obss[i], 0.5, 1.0, 4, X1)
         torch.cuda.synchronize()
         assert torch.equal(Xs[i], X1)
+    largest = max(range(len(shapes)), key=lambda i: shapes[i]["I1"] * shapes[i]["I2"])
+    first64 = next(i for i, sh in enumerate(shapes) if sh["trailing"][1] == 64)
+    for i in (largest, first64):
+        sh = shapes[i]
+        full = (sh["I1"], sh["I2"]) + sh["trailing"]
+        m, o = host[i]
+        ref, _ = O.pga(m, o, 0.5, 1.0, 4, [O.dct_matrix(n) for n in sh["trailing"]])
+        err = rel(from_dev(Xs[i], full), ref)
+        print(f"batch problem {i} {full} prec {prec}: rel err vs oracle {err:.2e}")
+        assert err <= 1e-5
