@@ -11,17 +11,24 @@ value     PGA iterations per second of the plain FP64 path, summed over ranks, i
           resident in HBM.  L2 is flushed (a 512 MiB write) between timed steps.
 e2e       the same metric through the C ABI with host buffers: the pinned-host mask and
           observations are copied in and the result copied out inside every step.
-mixed     the LT_MIXED path on the same inputs (FP32 data; modes below 64 stay in the
-          fused SIMT transform passes, so here it runs the FP32 kernels), with its
-          relative error against the FP64 result of the same run; fp32: the same for
-          the LT_FP32 context.
+mixed     the LT_MIXED path on the same inputs with the library's defaults (FP32 data;
+          modes below 64 stay in the fused SIMT transform passes, so on this workload it
+          runs the FP32 kernels: tc_launches_per_step = 0), with its relative error
+          against the FP64 result of the same run; mixed_tc32: LT_MIXED with the mode-32
+          products on the tcgen05 tensor cores (LT_OPT_TC_MODE_MIN = 32); fp32: the same
+          for the LT_FP32 context.
+svt       L-SVT slices/s (lt_svt, transforms included, and the Jacobi launch alone):
+          the 96 144x176 slices of P_Omega(M) (FP64, FP32) and the 2048 256x256 slices
+          of the fifth-order tensor (FP64, FP32, LT_MIXED) with errors against FP64.
 batched   the 64 uneven completion problems in LT_MIXED (those with I4 = 64 put their
           mode-4 products on the tcgen05 tensor cores) as one graph-captured call.
 product_256x256x16x16x8  the fifth-order *_L-product (LT_MIXED and FP32): the face-wise
-          GEMM on the tcgen05 tensor cores (split TF32 x 3) against the HBM roofline.
+          GEMM on the tcgen05 tensor cores (split TF32 x 3) against the HBM roofline,
+          and the error of each against the FP64 product of the same operands.
 roofline  the Jacobi SVT kernel (dominant): executed-flop count reported by the kernel
-          / its CUDA-event time over the timed steps, against the FP64 FMA peak measured
-          on this GPU (ALU-bound: the FP64 pipe).
+          / its CUDA-event time over the timed steps, against the FP64 FMA peak derived
+          from SMs x max SM clock x 2 DFMA/clk/SM (ALU-bound: the FP64 pipe), with the
+          fraction of the throughput lt_measure_fma_peak measures at start-up beside it.
 autotune  the SVT kernel form each context runs, picked by lt_autotune_svt (timings of
           every form on the observations, outside the timed region).
 cpu_baseline  the FP64 oracle (numpy/LAPACK) on the host cores, a bounded sample of
@@ -49,21 +56,55 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PGA iters/s & L-SVT slices/s, mixed vs FP64 at rel-err<=1e-5; %roofline"
 WORKLOAD = "pga_completion_144x176x3x32_fp64"
-# FMA throughput of the GPU in GFLOP/s, measured at start-up by lt_measure_fma_peak
-# (eight independent FMA chains per thread, four 512-thread CTAs per SM): the peaks of
-# the ALU-bound rooflines.
+# Peaks of the ALU-bound rooflines in GFLOP/s, derived from unit counts and clocks:
+# SMs x maximum SM clock x FMA units per SM per clock x 2 (FP64: 2 DFMA per SM per clock,
+# the part's nominal 1.25 TFLOP/s; FP32: 128 FFMA).  Beside them, the FMA throughput
+# that lt_measure_fma_peak measures at start-up (eight independent FMA chains per
+# thread, four 512-thread CTAs per SM): on GB300 FP32 reaches 97.6 % of the derived peak
+# and FP64 84 % (1057.8 GFLOP/s at 2070 MHz, the same for every chain, unroll and
+# occupancy variant tried).
+FMA_PER_CLK = {"fp64": 2, "fp32": 128}
 FMA_PEAKS = {}
-PEAK_SOURCE = ("lt_measure_fma_peak on this GPU at start-up (FMA chains, 4 x 512 threads "
-               "per SM, 3 timed launches; of measured)")
+DERIVED_PEAKS = {}
+PEAK_SOURCE = ("derived: SMs x max SM clock x FMA per SM per clock x 2 (FP64 2, FP32 128 "
+               "FMA/clk/SM); measured_peak = lt_measure_fma_peak at start-up")
+
+
+def max_sm_mhz():
+    try:
+        r = subprocess.run(["nvidia-smi", "-i", str(int(os.environ.get("LOCAL_RANK", "0"))),
+                            "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                           capture_output=True, text=True, timeout=20)
+        return float(r.stdout.strip().splitlines()[0])
+    except Exception:
+        return 2070.0
 
 
 def fma_peak(name):
-    """Measured FMA peak ("fp64" or "fp32") in GFLOP/s (cached)."""
+    """Derived FMA peak ("fp64" or "fp32") of this GPU in GFLOP/s (cached)."""
+    if name not in DERIVED_PEAKS:
+        import torch
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        DERIVED_PEAKS[name] = round(sms * max_sm_mhz() * 1e6 * FMA_PER_CLK[name] * 2 / 1e9, 1)
+    return DERIVED_PEAKS[name]
+
+
+def measured_peak(name):
+    """FMA throughput measured by lt_measure_fma_peak ("fp64" or "fp32"), GFLOP/s."""
     if name not in FMA_PEAKS:
         from paper_2202_02870_gb300 import lt
         prec = lt.LT_FP64 if name == "fp64" else lt.LT_FP32
         FMA_PEAKS[name] = round(max(lt.lt_measure_fma_peak(prec) for _ in range(2)), 1)
     return FMA_PEAKS[name]
+
+
+def alu_roofline(achieved, name, **extra):
+    """Roofline entry of an ALU-bound kernel: achieved GFLOP/s against the derived peak,
+    with the fraction of the measured FMA throughput beside it."""
+    peak, meas = fma_peak(name), measured_peak(name)
+    return dict({"bound": "alu", "achieved": round(achieved, 2), "peak": peak, "unit": "GFLOP/s",
+                 "frac": round(achieved / peak, 4), "peak_source": PEAK_SOURCE,
+                 "measured_peak": meas, "frac_of_measured": round(achieved / meas, 4)}, **extra)
 ORACLE_ITERS_PER_STEP = 3
 
 
@@ -265,8 +306,9 @@ def run_ours(args):
         return ctx
 
     tune(ctx64, obs64, "fp64")
-    fma_peak("fp64")
-    fma_peak("fp32")
+    for name in ("fp64", "fp32"):
+        fma_peak(name)
+        measured_peak(name)
 
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -327,9 +369,14 @@ def run_ours(args):
 
     # ---------------- FP32 and mixed (LT_MIXED: tensor-core mode-32 passes) paths on the
     # same inputs
-    def single_leg(prec, label):
-        ctxp = tune(ctx_for(prec), obs32, {lt.LT_FP32: "fp32", lt.LT_MIXED: "mixed"}[prec])
-        Xp, msp, _, stp, _ = run_path(ctxp, obs32, torch.float32, args.steps, args.warmup, True)
+    def single_leg(prec, label, tc_mode_min=None):
+        name = {lt.LT_FP32: "fp32", lt.LT_MIXED: "mixed"}[prec]
+        ctxp = ctx_for(prec)
+        if tc_mode_min is not None:
+            lt.lt_ctx_set_option(ctxp, lt.LT_OPT_TC_MODE_MIN, tc_mode_min)
+            name += f"_tc{tc_mode_min}"
+        ctxp = tune(ctxp, obs32, name)
+        Xp, msp, _, stp, repp = run_path(ctxp, obs32, torch.float32, args.steps, args.warmup, True)
         mean_ms = statistics.mean(msp)
         relp = float(torch.linalg.norm(Xp.double() - X64) / torch.linalg.norm(X64))
         jp = stp["jacobi"]
@@ -343,13 +390,18 @@ def run_ours(args):
                 "svt_slices_per_s": round(96 / (jp_ms / 1e3), 1) if jp_ms > 0 else None,
                 "transform_ms_per_step": round(tr["ms"] / args.steps, 3),
                 "tc_launches_per_step": stp["tc_launches"] / args.steps,
-                "roofline": {"kernel": "jacobi_svt (FP32)", "bound": "alu",
-                             "achieved": round(jp_ach, 1), "peak": fma_peak("fp32"),
-                             "unit": "GFLOP/s", "frac": round(jp_ach / fma_peak("fp32"), 4),
-                             "peak_source": PEAK_SOURCE}}
+                "max_sweeps": repp.max_sweeps_used,
+                "jacobi_flops_per_launch": jp_flops,
+                "roofline": alu_roofline(jp_ach, "fp32", kernel="jacobi_svt (FP32)")}
 
     fp32_leg = single_leg(lt.LT_FP32, "f32")
-    mixed_leg = single_leg(lt.LT_MIXED, "f32 + split-tf32x3 tensor cores")
+    # LT_MIXED with the library's defaults: modes 3 and 32 are below LT_OPT_TC_MODE_MIN
+    # (64), so this workload runs the FP32 kernels (tc_launches_per_step = 0)
+    mixed_leg = single_leg(lt.LT_MIXED, "f32 (LT_MIXED defaults: no mode of this workload "
+                                        "reaches the tensor cores)")
+    # LT_MIXED with the mode-32 products on the tcgen05 tensor cores (split TF32 x 3)
+    mixed_tc_leg = single_leg(lt.LT_MIXED, "f32 + mode-32 products on the tensor cores "
+                                           "(split tf32x3)", tc_mode_min=32)
 
     # ---------------- the Fourier operator (TNN-PGA-F, Sec. 5) on the same observations
     fourier = None
@@ -434,25 +486,26 @@ def run_ours(args):
                        "parallelism": f"replicas x{ws}"},
             "svt_slices_per_s": round(slices_per_s, 1),
             "mixed": mixed_leg,
+            "mixed_tc32": mixed_tc_leg,
             "fp32": fp32_leg,
             "autotune": tuned,
-            "fma_peaks_gflops": dict(FMA_PEAKS, source=PEAK_SOURCE),
+            "fma_peaks_gflops": {"derived": DERIVED_PEAKS, "measured": FMA_PEAKS,
+                                 "source": PEAK_SOURCE},
             "batched": batched,
             "fourier": fourier,
             "product_256x256x16x16x8": product,
             "svt": svt,
-            "roofline": {"kernel": "jacobi_svt (FP64)", "bound": "alu",
-                         "achieved": round(achieved, 2), "peak": fma_peak("fp64"),
-                         "unit": "GFLOP/s", "frac": round(achieved / fma_peak("fp64"), 4),
-                         "peak_source": PEAK_SOURCE,
-                         "traffic": profiled_traffic("jacobi_svt_fp64"),
-                         "flops_per_launch": jac_flops_avg, "ms_per_launch": round(jac_ms_avg, 4)},
+            "roofline": alu_roofline(achieved, "fp64", kernel="jacobi_svt (FP64)",
+                                     traffic=profiled_traffic("jacobi_svt_fp64"),
+                                     flops_per_launch=jac_flops_avg,
+                                     ms_per_launch=round(jac_ms_avg, 4)),
             "kernels": {f: {"launches": st64[f]["launches"], "ms": round(st64[f]["ms"], 3),
                             "share": round(st64[f]["ms"] / max(sum(st64[x]["ms"] for x in families), 1e-9), 4)}
                         for f in families},
             "transform_roofline": {
                 "bound": "alu", "achieved": round(tra["flops"] / max(tra["ms"], 1e-9) / 1e6, 2),
-                "unit": "GFLOP/s", "peak": fma_peak("fp64"),
+                "unit": "GFLOP/s", "peak": fma_peak("fp64"), "frac": round(
+                    tra["flops"] / max(tra["ms"], 1e-9) / 1e6 / fma_peak("fp64"), 4),
                 "hbm_gbs": round(tra["bytes"] / max(tra["ms"], 1e-9) / 1e6, 1),
                 "hbm_peak_gbs": hbm_peak()[0]},
             "e2e": {"value": round(job_rate(iters, ws, e2e_step), 5), "unit": "iters/s",
@@ -543,14 +596,11 @@ def fourier_leg(args, dev, ws, mask_d, obs64, c, flush, cpu):
         step_ms = max_over_ranks(statistics.mean(ms), ws, dev)
         jac = stats["jacobi"]
         gflops = jac["flops"] / max(jac["ms"], 1e-9) / 1e6
-        peak = fma_peak("fp64" if prec == lt.LT_FP64 else "fp32")
         leg = {"value": round(job_rate(iters, ws, step_ms), 4), "unit": "iters/s",
                "ms_per_iter": round(step_ms / iters, 3),
                "jacobi_ms_per_iter": round(jac["ms"] / max(args.fourier_steps * iters, 1), 3),
-               "roofline": {"kernel": f"jacobi_svt ({label.upper()})", "bound": "alu",
-                            "achieved": round(gflops, 1), "peak": peak, "unit": "GFLOP/s",
-                            "frac": round(gflops / peak, 4),
-                            "peak_source": PEAK_SOURCE},
+               "roofline": alu_roofline(gflops, "fp64" if prec == lt.LT_FP64 else "fp32",
+                                        kernel=f"jacobi_svt ({label.upper()})"),
                "rel_residual": rep.rel_residual, "device_status": rep.device_status}
         if X64 is None:
             X64 = X.double()
@@ -572,52 +622,98 @@ def fourier_leg(args, dev, ws, mask_d, obs64, c, flush, cpu):
 
 def run_batched_leg(args, dev, ws):
     """The 64 independent completion problems of uneven sizes (I1 x I2 from 64 x 48 to
-    512 x 384, I3 = 3, I4 in {8, 16, 32, 64}, DCT transforms), LT_MIXED: one
-    lt_pga_complete_batched call (a CUDA graph with a branch per problem) of `iters`
-    iterations per step, against the same problems issued one after the other."""
+    512 x 384, I3 = 3, I4 in {8, 16, 32, 64}, DCT transforms) as one
+    lt_pga_complete_batched call (a CUDA graph with a branch per problem):
+    mixed  LT_MIXED, `--batched-iters` iterations per call, `--batched-steps` timed
+           calls after one warm-up call, against the same problems issued one after the
+           other; the Jacobi flops the kernels counted over the wall time against the
+           derived FP32 FMA peak;
+    fp64   the same problems in FP64, `--batched-iters-fp64` iterations, one timed call
+           (no warm-up: a call takes seconds), and the relative error of the mixed
+           iterates against the FP64 ones after the same iterations."""
     import torch
     from paper_2202_02870_gb300 import lt, synth
     shapes = synth.config4_shapes()
     rng = np.random.default_rng(4)
-    ctxs, masks, obss, Xs = [], [], [], []
+    masks, obs64 = [], []
     elems = 0
     for sh in shapes:
         full = (sh["I1"], sh["I2"]) + sh["trailing"]
         elems += int(np.prod(full))
-        ctxs.append(lt.Context(list(sh["trailing"]), [lt.lt_make_dct(n) for n in sh["trailing"]],
-                               lt.LT_MIXED))
         m = torch.from_numpy((rng.random(int(np.prod(full))) < sh["rho"]).astype(np.uint8))
         masks.append(m.reshape(tuple(reversed(full))).to(dev))
-        obss.append(masks[-1].float() * torch.randn(tuple(reversed(full)), device=dev))
-        Xs.append(torch.zeros(tuple(reversed(full)), dtype=torch.float32, device=dev))
-    n = len(ctxs)
-    iters = args.batched_iters
-    wsb = torch.empty(lt.lt_workspace_size_batched(ctxs, [x.shape[-1] for x in Xs],
-                                                   [x.shape[-2] for x in Xs]),
-                      dtype=torch.uint8, device=dev)
-    run = lambda: lt.lt_pga_complete_batched(ctxs, masks, obss, [0.5] * n, [1.0] * n, iters, Xs, ws=wsb)
-    run()
-    torch.cuda.synchronize()
-    st = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(args.batched_steps):
-        run()
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_b = e0.elapsed_time(e1) / args.batched_steps
-    # the same work, one problem after the other on one stream
-    e0.record(st)
-    for i in range(n):
-        lt.lt_pga_complete(ctxs[i], masks[i], obss[i], 0.5, 1.0, iters, Xs[i])
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_s = e0.elapsed_time(e1)
-    return {"problems": n, "elements": elems, "iters_per_step": iters,
-            "dtype": "f32 + split-tf32x3 tensor cores",
-            "value": round(ws * n * iters / (ms_b / 1e3), 2), "unit": "problem-iters/s",
-            "ms_per_step": round(ms_b, 2), "sequential_ms": round(ms_s, 2),
-            "speedup_vs_sequential": round(ms_s / ms_b, 3)}
+        obs64.append(masks[-1].double() * torch.randn(tuple(reversed(full)), device=dev,
+                                                      dtype=torch.float64))
+    n = len(shapes)
+    out = {"problems": n, "elements": elems}
+    finals = {}
+    for name, prec, dt in (("mixed", lt.LT_MIXED, torch.float32), ("fp64", lt.LT_FP64, torch.float64)):
+        iters = args.batched_iters if name == "mixed" else args.batched_iters_fp64
+        steps = args.batched_steps if name == "mixed" else 1
+        ctxs = [lt.Context(list(sh["trailing"]), [lt.lt_make_dct(k) for k in sh["trailing"]], prec)
+                for sh in shapes]
+        obss = [o.to(dt) for o in obs64]
+        Xs = [torch.zeros_like(o) for o in obss]
+        wsb = torch.empty(lt.lt_workspace_size_batched(ctxs, [x.shape[-1] for x in Xs],
+                                                       [x.shape[-2] for x in Xs]),
+                          dtype=torch.uint8, device=dev)
+
+        def run():
+            for x in Xs:
+                x.zero_()
+            lt.lt_pga_complete_batched(ctxs, masks, obss, [0.5] * n, [1.0] * n, iters, Xs, ws=wsb)
+
+        if name == "mixed":
+            run()
+        torch.cuda.synchronize()
+        for cx in ctxs:
+            lt.lt_ctx_get_stats(cx, reset=True)
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            run()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms_b = e0.elapsed_time(e1) / steps
+        flops = sum(lt.lt_ctx_get_stats(cx, reset=True)["jacobi"]["flops"] for cx in ctxs) / steps
+        leg = {"dtype": "f32 + split-tf32x3 tensor cores (I4 = 64 problems' mode-4 products)"
+                        if name == "mixed" else "f64",
+               "iters_per_step": iters, "steps": steps,
+               "value": round(ws * n * iters / (ms_b / 1e3), 3), "unit": "problem-iters/s",
+               "ms_per_step": round(ms_b, 2),
+               "jacobi_roofline": alu_roofline(
+                   flops / (ms_b / 1e3) / 1e9, "fp32" if name == "mixed" else "fp64",
+                   note="Jacobi flops counted by the kernels over the whole batch call's "
+                        "wall time")}
+        if name == "mixed":
+            # the same work, one problem after the other on one stream
+            e0.record(st)
+            for i in range(n):
+                Xs[i].zero_()
+                lt.lt_pga_complete(ctxs[i], masks[i], obss[i], 0.5, 1.0, iters, Xs[i])
+            e1.record(st)
+            torch.cuda.synchronize()
+            ms_s = e0.elapsed_time(e1)
+            leg["sequential_ms"] = round(ms_s, 2)
+            leg["speedup_vs_sequential"] = round(ms_s / ms_b, 3)
+            if args.batched_iters_fp64 != iters:
+                # the mixed iterates at the FP64 leg's iteration count, for the error
+                for x in Xs:
+                    x.zero_()
+                lt.lt_pga_complete_batched(ctxs, masks, obss, [0.5] * n, [1.0] * n,
+                                           args.batched_iters_fp64, Xs, ws=wsb)
+                torch.cuda.synchronize()
+        finals[name] = [x.double() for x in Xs]
+        out[name] = leg
+        del ctxs, obss, Xs, wsb
+        torch.cuda.empty_cache()
+    num = sum(float(torch.linalg.norm(a - b) ** 2) for a, b in zip(finals["mixed"], finals["fp64"]))
+    den = sum(float(torch.linalg.norm(b) ** 2) for b in finals["fp64"])
+    out["mixed"]["rel_err_vs_fp64"] = (num / den) ** 0.5
+    out["mixed"]["rel_err_iters"] = args.batched_iters_fp64
+    out["mixed_over_fp64"] = round(out["mixed"]["value"] / out["fp64"]["value"], 2)
+    return out
 
 
 def svt_rate(ctx, G, tau, D, wsb, units, steps, warmup, flush):
@@ -673,11 +769,7 @@ def svt_legs(dev, obs64, c, flush, steps):
         wsb = torch.empty(max(lt.lt_workspace_size(ctx, lt.LT_OP_SVT, 144, 176), 1),
                           dtype=torch.uint8, device=dev)
         leg = svt_rate(ctx, G, c["tau"], D, wsb, 96, steps, 2, flush)
-        peak = fma_peak(name)
-        leg["jacobi_roofline"] = {"bound": "alu", "achieved": leg["jacobi_gflops_executed"],
-                                  "peak": peak, "unit": "GFLOP/s",
-                                  "frac": round(leg["jacobi_gflops_executed"] / peak, 4),
-                                  "peak_source": PEAK_SOURCE}
+        leg["jacobi_roofline"] = alu_roofline(leg["jacobi_gflops_executed"], name)
         out["config2_144x176x3x32"][name] = leg
     c3 = synth.config3()
     mats3 = [np.asarray(m) for _, m in c3["transforms"]]
@@ -700,11 +792,8 @@ def svt_legs(dev, obs64, c, flush, steps):
                           dtype=torch.uint8, device=dev)
         n = 1 if prec == lt.LT_FP64 else max(1, min(steps, 3))
         leg = svt_rate(ctx, G, tau3, D, wsb, 2048, n, 1, flush)
-        peak = fma_peak("fp64" if prec == lt.LT_FP64 else "fp32")
-        leg["jacobi_roofline"] = {"bound": "alu", "achieved": leg["jacobi_gflops_executed"],
-                                  "peak": peak, "unit": "GFLOP/s",
-                                  "frac": round(leg["jacobi_gflops_executed"] / peak, 4),
-                                  "peak_source": PEAK_SOURCE}
+        leg["jacobi_roofline"] = alu_roofline(leg["jacobi_gflops_executed"],
+                                              "fp64" if prec == lt.LT_FP64 else "fp32")
         leg["device_status"] = lt.lt_last_device_status(ctx)
         if D64 is None:
             D64 = D.double()
@@ -953,6 +1042,33 @@ def run_pga5(args):
     for name in ("fp32", "mixed"):
         out[name]["rel_diff_vs_fp64"] = float(torch.linalg.norm(res[name] - res["fp64"]) /
                                               torch.linalg.norm(res["fp64"]))
+    if args.tol5 > 0:
+        # run to the stopping test of Sec. 5 (r <= tol) on the chosen path, from a cold
+        # start; FP64 time-to-residual extrapolated from its ms per iteration above
+        name = args.precision if args.precision != "fp64" else "mixed"
+        prec = {"fp32": lt.LT_FP32, "mixed": lt.LT_MIXED}[name]
+        ctx = lt.Context([3, 120], mats, prec)
+        obs = obs64.float()
+        X = torch.zeros(tshape, dtype=torch.float32, device=dev)
+        wsb = torch.empty(lt.lt_workspace_size(ctx, lt.LT_OP_PGA, 540, 960), dtype=torch.uint8,
+                          device=dev)
+        rep = lt.lt_pga_report()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        lt.lt_pga_complete(ctx, mask, obs, 0.5, 1.0, args.max_iters5, X, tol=args.tol5,
+                           report=rep, ws=wsb)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["to_residual"] = {
+            "path": name, "tol": args.tol5, "max_iters": args.max_iters5,
+            "iters_done": rep.iters_done, "rel_residual": rep.rel_residual,
+            "reached": bool(rep.rel_residual <= args.tol5), "device_status": rep.device_status,
+            "seconds": round(ms / 1e3, 3), "ms_per_iter": round(ms / max(rep.iters_done, 1), 2),
+            "fp64_seconds_extrapolated": round(out["fp64"]["ms_per_iter"] * rep.iters_done / 1e3, 2),
+            "fp64_note": "FP64 time per iteration measured over the first iterations above, "
+                         "times the iterations this path needed (extrapolated)"}
     print(json.dumps(out))
 
 
@@ -994,6 +1110,106 @@ def run_svt5(args):
                       "algorithmic_bytes_per_launch": j["bytes"] / max(j["launches"], 1),
                       "phase_ms_per_slice": {k: round(v / (3 * args.i4 * args.steps) / 1.97e6, 3)
                                              for k, v in st["jacobi_phase_cycles"].items()}}))
+
+
+def run_warmstart(args):
+    """--case warmstart: what a warm start of the SVT's Jacobi iteration would save in the
+    benchmark completion (Algorithm 5 on the 144x176x3x32 problem).  For iteration k,
+    G^k = Y^k - step P_Omega(Y^k - M) is formed from the checkpoint of the run after k - 1
+    iterations, and V^{k-1}, the right singular vectors of G^{k-1}, from lt_svd.  The
+    slices are 144 x 176, so the SVT kernel orthogonalises the columns of the transposed
+    slices, and the start a warm-started Jacobi would get is the left-rotated tensor
+    C^k = U^{k-1,T} *_L G^k (lt_product), U^{k-1} the left singular vectors of G^{k-1}
+    (lt_svd): transform-domain slices U_hat^{k-1,p,T} G_hat^{k,p}, the same singular
+    values as G^k, with the previous iteration's singular vectors already applied.  The
+    Jacobi launch of lt_svt on C^k against the one on G^k (CUDA events of the library,
+    median of --steps calls) measures the saving; U^{k-1} *_L D_tau(C^k) must equal
+    D_tau(G^k).  `ideal` applies G^k's own left singular vectors (the best any warm
+    start could do)."""
+    import torch
+    from paper_2202_02870_gb300 import lt
+    prec = {"fp64": lt.LT_FP64, "fp32": lt.LT_FP32, "mixed": lt.LT_MIXED}[args.precision]
+    dt = torch.float64 if prec == lt.LT_FP64 else torch.float32
+    c = problem_inputs(0)
+    dev = torch.device("cuda", 0)
+    shape = (144, 176, 3, 32)
+    tsh = tuple(reversed(shape))
+    to_dev = lambda a, t: torch.from_numpy(np.ascontiguousarray(a.ravel(order="F"))).to(t).reshape(
+        tuple(reversed(a.shape))).to(dev)
+    mats = [lt.lt_make_dct(3), lt.lt_make_dct(32)]
+    ctx64 = lt.Context([3, 32], mats, lt.LT_FP64)
+    Xt = torch.empty(tsh, dtype=torch.float64, device=dev)
+    lt.lt_product(ctx64, to_dev(c["U"], torch.float64),
+                  to_dev(np.asfortranarray(np.swapaxes(c["V"], 0, 1)), torch.float64), Xt)
+    mask = torch.from_numpy(np.ascontiguousarray(c["mask"].ravel(order="F"))).reshape(tsh).to(dev)
+    obs = (mask.double() * (Xt + to_dev(c["noise"], torch.float64))).to(dt)
+    ctx = ctx64 if prec == lt.LT_FP64 else lt.Context([3, 32], mats, prec)
+    tau, step = c["tau"], c["step"]
+
+    def g_after(j):
+        """G of iteration j + 1 from the state after j iterations of a cold run."""
+        X = torch.zeros(tsh, dtype=dt, device=dev)
+        prev = torch.zeros_like(X)
+        st = lt.lt_pga_state(X_prev=prev.data_ptr(), t_prev=1.0, t=1.0, k=0)
+        if j > 0:
+            lt.lt_pga_complete(ctx, mask, obs, tau, step, j, X, state=st)
+        torch.cuda.synchronize()
+        beta = (st.t_prev - 1.0) / st.t if j > 0 else 0.0
+        Y = X + beta * (X - prev)
+        return Y - step * mask.to(dt) * (Y - obs)
+
+    def jacobi_ms(G):
+        D = torch.empty_like(G)
+        for _ in range(2):
+            lt.lt_svt(ctx, G, tau * step, D)
+        torch.cuda.synchronize()
+        lt.lt_ctx_get_stats(ctx, reset=True)
+        lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 1)
+        per = []
+        for _ in range(args.steps):
+            lt.lt_svt(ctx, G, tau * step, D)
+            per.append(lt.lt_ctx_get_stats(ctx, reset=True)["jacobi"]["ms"])
+        lt.lt_ctx_set_option(ctx, lt.LT_OPT_PROFILE, 0)
+        return statistics.median(per), D
+
+    def left_vectors(G):
+        U = torch.empty((32, 3, 144, 144), dtype=dt, device=dev)
+        S = torch.empty_like(G)
+        V = torch.empty((32, 3, 176, 176), dtype=dt, device=dev)
+        lt.lt_svd(ctx, G, U, S, V)
+        return U
+
+    def transpose(V):  # L-transpose: swap modes 1 and 2 (real transforms)
+        return V.transpose(-1, -2).contiguous()
+
+    out = {"case": "warmstart", "precision": args.precision, "iterations": {}}
+    for k in args.warm_iters:
+        Gp, Gk = g_after(k - 2), g_after(k - 1)
+        Up, Uk = left_vectors(Gp), left_vectors(Gk)
+        UpT, UkT = transpose(Up), transpose(Uk)
+        Cw = torch.empty_like(Gk)
+        Ci = torch.empty_like(Gk)
+        lt.lt_product(ctx, UpT, Gk, Cw)
+        lt.lt_product(ctx, UkT, Gk, Ci)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            lt.lt_product(ctx, UpT, Gk, Cw)
+        e1.record()
+        torch.cuda.synchronize()
+        prod_ms = e0.elapsed_time(e1) / args.steps
+        cold, Dc = jacobi_ms(Gk)
+        warm, Dw = jacobi_ms(Cw)
+        ideal, _ = jacobi_ms(Ci)
+        back = torch.empty_like(Dw)
+        lt.lt_product(ctx, Up, Dw, back)
+        torch.cuda.synchronize()
+        out["iterations"][k] = {
+            "jacobi_ms_cold": round(cold, 3), "jacobi_ms_warm": round(warm, 3),
+            "jacobi_ms_ideal": round(ideal, 3), "warm_over_cold": round(warm / cold, 3),
+            "rotation_product_ms": round(prod_ms, 3),
+            "svt_agreement": float(torch.linalg.norm(back - Dc) / torch.linalg.norm(Dc))}
+    print(json.dumps(out))
 
 
 def run_reference(args):
@@ -1040,6 +1256,8 @@ def main():
                     help="timed calls of the 64-problem batch (0 skips the batched leg)")
     ap.add_argument("--batched-iters", type=int, default=4,
                     help="PGA iterations per call of the 64-problem batch")
+    ap.add_argument("--batched-iters-fp64", type=int, default=2,
+                    help="PGA iterations of the FP64 call of the 64-problem batch")
     ap.add_argument("--fourier-steps", type=int, default=2,
                     help="timed steps of the Fourier-operator (TNN-PGA-F) leg; 0 skips it")
     ap.add_argument("--fourier-iters", type=int, default=10,
@@ -1048,13 +1266,20 @@ def main():
                     help="timed calls per precision of the L-SVT legs (0 skips them)")
     ap.add_argument("--product-steps", type=int, default=5,
                     help="timed calls of the fifth-order product leg (0 skips it)")
+    ap.add_argument("--warm-iters", type=int, nargs="+", default=[3, 10, 30, 60, 99],
+                    help="--case warmstart: PGA iterations k at which G^k is measured")
     ap.add_argument("--i4", type=int, default=40,
                     help="mode-4 size of --case svt5 (slices = 3 * i4)")
     ap.add_argument("--iters5", type=int, default=3,
                     help="PGA iterations per path of --case pga5")
+    ap.add_argument("--tol5", type=float, default=0.0,
+                    help="--case pga5: also run --precision (fp32 or mixed) from a cold "
+                         "start until the relative residual is <= this value")
+    ap.add_argument("--max-iters5", type=int, default=300,
+                    help="--case pga5: iteration cap of the --tol5 run")
     ap.add_argument("--case", default="pga",
                     choices=["pga", "svt", "product", "product5", "transform5", "pga5",
-                             "svt5"],
+                             "svt5", "warmstart"],
                     help="pga: the benchmark line; svt/product: single-operation runs "
                          "used for profiling")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
@@ -1084,6 +1309,9 @@ def main():
         return
     if args.case == "svt5":
         run_svt5(args)
+        return
+    if args.case == "warmstart":
+        run_warmstart(args)
         return
     if args.case != "pga":
         run_case(args)
