@@ -8,7 +8,9 @@ forward transform, per-slice Jacobi SVD + shrink + reconstruction, inverse trans
 with the fused residual, device-side scalar update.
 
 value     PGA iterations per second of the plain FP64 path, summed over ranks, inputs
-          resident in HBM.  L2 is flushed (a 512 MiB write) between timed steps.
+          resident in HBM.  L2 is flushed (a 512 MiB write) between timed steps.  The
+          completion contexts run with the warm-started SVT (LT_OPT_WARM_START: period 8
+          for FP64, 4 for FP32 / LT_MIXED; --warm / --warm32, 0 turns it off).
 e2e       the same metric through the C ABI with host buffers: the pinned-host mask and
           observations are copied in and the result copied out inside every step.
 mixed     the LT_MIXED path on the same inputs with the library's defaults (FP32 data;
@@ -274,6 +276,9 @@ def run_ours(args):
 
     def ctx_for(prec):
         ctx = lt.Context([3, 32], [lt.lt_make_dct(3), lt.lt_make_dct(32)], prec)
+        warm = args.warm if prec == lt.LT_FP64 else args.warm32
+        if warm:
+            lt.lt_ctx_set_option(ctx, lt.LT_OPT_WARM_START, warm)
         return ctx
 
     ctx64 = ctx_for(lt.LT_FP64)
@@ -482,6 +487,7 @@ def run_ours(args):
                     "paper's colour videos",
             "config": {"workload": WORKLOAD, "shape": [144, 176, 3, 32], "transforms": ["dct3", "dct32"],
                        "tau": 0.5, "step": 1.0, "iters_per_step": iters, "rank": 10, "observed": 0.3,
+                       "warm_start_period": {"fp64": args.warm, "fp32_mixed": args.warm32},
                        "l2": "flushed between steps (512 MiB write)",
                        "parallelism": f"replicas x{ws}"},
             "svt_slices_per_s": round(slices_per_s, 1),
@@ -1250,6 +1256,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--warm", type=int, default=8,
+                    help="LT_OPT_WARM_START period of the FP64 completion context (0: off)")
+    ap.add_argument("--warm32", type=int, default=4,
+                    help="LT_OPT_WARM_START period of the FP32 / LT_MIXED completion contexts")
     ap.add_argument("--cpu-iters", type=int, default=15)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--batched-steps", type=int, default=2,

@@ -134,11 +134,26 @@ typedef enum {
                                 LT_DEV_TIMEOUT, stops issuing work, drains the copies and
                                 products it has in flight, frees its TMEM and returns;
                                 its output is then undefined. */
-  LT_OPT_TC_TEST_NO_LOADS = 12 /* LT_MIXED, for testing the timeout path only: 1 = the
+  LT_OPT_TC_TEST_NO_LOADS = 12, /* LT_MIXED, for testing the timeout path only: 1 = the
                                 tensor-core kernel's producer issues no copies, so the
                                 other roles' first waits expire after LT_OPT_TC_WAIT_US
                                 and every call that reaches the kernel reports
                                 LT_DEV_TIMEOUT with undefined output; 0 (default) = off */
+  LT_OPT_WARM_START = 13     /* lt_pga_complete (real transforms): 0 (default) = every
+                                iteration's SVT starts from scratch; p >= 2 = warm start
+                                with period p.  Iteration j of a call (j = 0, 1, ...) with
+                                j % p == 0 thresholds L(G)^p from scratch and keeps the
+                                orthonormal basis Q of the side the Jacobi kernel
+                                orthogonalises (left singular vectors when I1 < I2, else
+                                right ones); the other iterations threshold Q^T L(G)^p (or
+                                L(G)^p Q), which starts near its converged form and takes
+                                fewer sweeps, and map the result back (the SVT is
+                                unitarily invariant), updating Q.  The cold iterations
+                                bound the loss of orthogonality of the accumulated Q.
+                                Needs 3 n^2 P elements + n P ints + one tensor more of
+                                workspace (n = min(I1, I2); lt_workspace_size with
+                                LT_OP_PGA includes them once the option is set).  The
+                                batched call and Fourier contexts ignore it. */
 } lt_option;
 
 /* Kernel families counted by lt_ctx_get_stats. */

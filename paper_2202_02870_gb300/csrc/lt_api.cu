@@ -245,6 +245,11 @@ cudaError_t run_fourier_svt(Ctx& c, const FourierSvt& F, int64_t I1, int64_t I2,
 // ---- workspace layouts ---------------------------------------------------------------
 struct PgaLayout {
   size_t x2, ghat, partials, scal, info, jac, total;
+  // warm start (LT_OPT_WARM_START): two bases Q (n x n per slice), the kernel's basis W
+  // and permutation, and the rotated slices C
+  bool warm = false;
+  int64_t wn = 0;
+  size_t qa = 0, qb = 0, wb = 0, wperm = 0, cbuf = 0;
   lt::TransformPlan fwd, inv;
   lt::JacobiPlan jp;
   FourierSvt fz;                      // Fourier contexts: the SVT's plans and region
@@ -270,6 +275,17 @@ lt_status pga_layout(const Ctx& c, int64_t I1, int64_t I2, PgaLayout* L) {
   L->scal = off; off += align256(sizeof(lt::PgaScalars));
   L->info = off; off += align256((size_t)c.P * sizeof(lt::SliceInfo));
   L->jac = off; off += align256(c.fourier_n ? L->fz.total : L->jp.ws_bytes);
+  L->warm = c.warm_period >= 2 && !c.fourier_n;
+  if (L->warm) {
+    const int64_t n = std::min(I1, I2);
+    const size_t qbytes = align256((size_t)n * n * c.P * c.elem);
+    L->wn = n;
+    L->qa = off; off += qbytes;
+    L->qb = off; off += qbytes;
+    L->wb = off; off += qbytes;
+    L->wperm = off; off += align256((size_t)n * c.P * sizeof(int));
+    L->cbuf = off; off += align256((size_t)N * c.elem);
+  }
   L->total = off;
   return LT_OK;
 }
@@ -504,6 +520,11 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
     case LT_OPT_NU:
       if (!(value > 0.0 && value <= 1.0)) return LT_ERR_ARG;
       c->nu = value;
+      return LT_OK;
+    case LT_OPT_WARM_START:
+      if (!(value == 0 || (value >= 2 && value <= 1e6)) || value != std::floor(value))
+        return LT_ERR_ARG;
+      c->warm_period = (int)value;
       return LT_OK;
     case LT_OPT_TC_WAIT_US:
       if (!(value >= 0.0 && value <= 60e6)) return LT_ERR_ARG;
@@ -797,6 +818,12 @@ struct PgaRun {
   lt::JacobiIO io;
   double fwd_bytes, inv_bytes, fwd_flops, inv_flops;
   int rows;
+  // warm start: buffers (null when off) and which basis is current
+  void* Q[2] = {nullptr, nullptr};
+  void* Wb = nullptr;
+  int* Wperm = nullptr;
+  void* Cb = nullptr;
+  int qcur = 0;
 };
 
 lt_status pga_prepare(Ctx& c, int64_t I1, int64_t I2, const uint8_t* mask, const void* obs,
@@ -841,6 +868,13 @@ lt_status pga_prepare(Ctx& c, int64_t I1, int64_t I2, const uint8_t* mask, const
   r->fwd_flops = transform_flops(r->L.fwd, I1 * I2, c.P) + 6 * Nd;
   r->inv_flops = transform_flops(r->L.inv, I1 * I2, c.P) + 7 * Nd;
   r->rows = r->L.max_rows;
+  if (r->L.warm) {
+    r->Q[0] = w + r->L.qa;
+    r->Q[1] = w + r->L.qb;
+    r->Wb = w + r->L.wb;
+    r->Wperm = reinterpret_cast<int*>(w + r->L.wperm);
+    r->Cb = w + r->L.cbuf;
+  }
   return LT_OK;
 }
 
@@ -856,11 +890,87 @@ cudaError_t pga_begin(PgaRun& r, const lt_pga_state* state, double tol, cudaStre
   return e;
 }
 
-// Iteration j of the run: fused forward transform, Jacobi SVT, fused inverse transform,
-// scalar update.  `account` is false while the launches are being captured into a graph
-// (they are then counted per replay).
-cudaError_t pga_iteration(PgaRun& r, int64_t j, cudaStream_t st, bool account) {
+// The SVT step of a warm-started iteration (LT_OPT_WARM_START): with Q the basis of the
+// previous iteration (n = min(I1, I2), n x n per slice) the Jacobi kernel thresholds
+// C = Q^T G_hat (I1 < I2: the kernel orthogonalises the columns of the transposed slice)
+// or C = G_hat Q, the result goes back as D_hat = Q D_tau(C) or D_tau(C) Q^T (the SVT is
+// unitarily invariant), and the next basis is Q P W from the kernel's basis W and QR
+// permutation P.  A cold iteration thresholds G_hat itself and starts the basis as P W.
+cudaError_t warm_svt(PgaRun& r, bool cold, cudaStream_t st, bool account) {
   Ctx& c = *r.c;
+  const int64_t I1 = r.I1, I2 = r.I2, n = r.L.wn, P = c.P;
+  const bool tr = I1 < I2;
+  const double eb = c.elem;
+  lt::JacobiIO io = r.io;
+  io.W = r.Wb;
+  io.Wperm = r.Wperm;
+  void* Q = r.Q[r.qcur];
+  void* Qn = r.Q[1 - r.qcur];
+  cudaError_t e = cudaSuccess;
+  const double slice_flops = 2.0 * (double)I1 * I2 * n * P;
+  const double slice_bytes = (2.0 * I1 * I2 + (double)n * n) * P * eb;
+  if (!cold) {
+    lt::StridedGemm g;  // C = Q^T G_hat or G_hat Q
+    g.P = P; g.M = I1; g.N = I2; g.K = n;
+    g.scm = 1; g.scn = I1; g.scp = I1 * I2;
+    const void *A, *B;
+    if (tr) {
+      A = Q; g.sam = n; g.sak = 1; g.sap = n * n;
+      B = r.Gh; g.sbk = 1; g.sbn = I1; g.sbp = I1 * I2;
+    } else {
+      A = r.Gh; g.sam = 1; g.sak = I1; g.sap = I1 * I2;
+      B = Q; g.sbk = 1; g.sbn = n; g.sbp = n * n;
+    }
+    Scope sc(c, st, LT_K_GEMM, account);
+    e = lt::launch_strided_gemm(c, g, A, B, r.Cb, r.scal, st);
+    sc.done(1, slice_flops, slice_bytes);
+    io.A = r.Cb;
+    io.D = r.Cb;
+  }
+  if (e == cudaSuccess) e = run_jacobi(c, r.L.jp, io, st, account);
+  if (e == cudaSuccess && !cold) {
+    lt::StridedGemm g;  // D_hat = Q D_tau(C) or D_tau(C) Q^T, into G_hat
+    g.P = P; g.M = I1; g.N = I2; g.K = n;
+    g.scm = 1; g.scn = I1; g.scp = I1 * I2;
+    const void *A, *B;
+    if (tr) {
+      A = Q; g.sam = 1; g.sak = n; g.sap = n * n;
+      B = r.Cb; g.sbk = 1; g.sbn = I1; g.sbp = I1 * I2;
+    } else {
+      A = r.Cb; g.sam = 1; g.sak = I1; g.sap = I1 * I2;
+      B = Q; g.sbk = n; g.sbn = 1; g.sbp = n * n;
+    }
+    Scope sc(c, st, LT_K_GEMM, account);
+    e = lt::launch_strided_gemm(c, g, A, B, r.Gh, r.scal, st);
+    sc.done(1, slice_flops, slice_bytes);
+  }
+  if (e == cudaSuccess) {
+    if (cold) {
+      Scope sc(c, st, LT_K_AUX, account);
+      e = lt::launch_warm_scatter(c, n, P, r.Wb, r.Wperm, Qn, r.scal, st);
+      sc.done(1, 0.0, 2.0 * (double)n * n * P * eb);
+    } else {
+      lt::StridedGemm g;  // next basis Q P W
+      g.P = P; g.M = n; g.N = n; g.K = n;
+      g.sam = 1; g.sak = n; g.sap = n * n; g.kperm = r.Wperm;
+      g.sbk = 1; g.sbn = n; g.sbp = n * n;
+      g.scm = 1; g.scn = n; g.scp = n * n;
+      Scope sc(c, st, LT_K_GEMM, account);
+      e = lt::launch_strided_gemm(c, g, Q, r.Wb, Qn, r.scal, st);
+      sc.done(1, 2.0 * (double)n * n * n * P, 3.0 * (double)n * n * P * eb);
+    }
+    r.qcur = 1 - r.qcur;
+  }
+  return e;
+}
+
+// Iteration j of the run: fused forward transform, Jacobi SVT, fused inverse transform,
+// scalar update.  allow_warm: the warm start may be used (not in captured batches).  `account` is false while the launches are being captured into a graph
+// (they are then counted per replay).
+cudaError_t pga_iteration(PgaRun& r, int64_t j, cudaStream_t st, bool account,
+                          bool allow_warm = false) {
+  Ctx& c = *r.c;
+  const bool warm = allow_warm && r.L.warm;
   void* cur = (j % 2 == 0) ? r.X : r.X2;
   void* old = (j % 2 == 0) ? r.X2 : r.X;
   r.f.x_cur = cur;
@@ -876,6 +986,7 @@ cudaError_t pga_iteration(PgaRun& r, int64_t j, cudaStream_t st, bool account) {
   if (e == cudaSuccess)
     e = c.fourier_n ? run_fourier_svt(c, r.L.fz, r.I1, r.I2, r.Gh, r.io.tau, r.io, r.io.scratch,
                                       st, account)
+        : warm      ? warm_svt(r, j % c.warm_period == 0, st, account)
                     : run_jacobi(c, r.L.jp, r.io, st, account);
   if (e == cudaSuccess) {
     Scope sc(c, st, LT_K_TRANSFORM, account);
@@ -953,7 +1064,7 @@ lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8_t* mas
     // continuation (Algorithm 5, mu_{k+1} = max(nu mu_k, mu_bar) with mu_bar = tau):
     // iteration k thresholds at step * max(nu^k mu_0, tau); off (mu_0 = 0): step * tau
     if (c.mu0 > 0.0) r.io.tau = step * std::max(std::pow(c.nu, (double)(k0 + j)) * c.mu0, tau);
-    e = pga_iteration(r, j, st, true);
+    e = pga_iteration(r, j, st, true, true);
   }
   if (e == cudaSuccess) e = pga_end(r, state, report, st);
   return cuda_status(e);

@@ -44,6 +44,8 @@ struct Ctx {
   int tc_tile_n = 0;                  // LT_MIXED: forced tensor-core tile width (0 = auto)
   double tc_wait_us = 0.0;            // LT_MIXED: tensor-core wait limit (0 = default 1 s)
   int tc_no_loads = 0;                // LT_MIXED test switch: no TMA copies are issued
+  int warm_period = 0;                // PGA warm start: 0 = off; p >= 2: iterations j with
+                                      // j % p == 0 (counted within a call) are cold
   double mu0 = 0.0;                   // PGA continuation: mu_0 (0 = off)
   double nu = 0.9;                    // PGA continuation: decay of mu
   mutable int64_t tc_launches = 0;    // tensor-core kernel launches (lt_ctx_get_stats)
@@ -210,10 +212,36 @@ struct JacobiIO {
   SliceInfo* info = nullptr;
   double* flops = nullptr;  // device counter of executed flops (atomic, per slice)
   double* phases = nullptr; // device: 10 phase cycle counters (profiling), or null
+  // SVT kernels, optional (warm start): per slice the n x n orthonormal basis of the
+  // orthogonalised side (n = min(I1, I2); column-major, row r in the QR order of the
+  // kernel) and the QR permutation (n entries); identity where the slice is rank
+  // deficient or did not converge
+  void* W = nullptr;
+  int* Wperm = nullptr;
 };
 
 cudaError_t launch_jacobi(const Ctx& c, const JacobiPlan& jp, const JacobiIO& io,
                           cudaStream_t st);
+
+// ----------------------------------------------------------------------------------
+// Warm start (lt_warm.cu): batched products with general element strides,
+//   C^p(m, n) = sum_k A^p(m, kk) B^p(k, n),  kk = kperm ? kperm[p K + k] : k,
+// A^p(m, k) = A[p sap + m sam + k sak], B^p(k, n) = B[p sbp + k sbk + n sbn],
+// C^p(m, n) = C[p scp + m scm + n scn]; and Q^p(perm[r], c) = W^p(r, c).
+// ----------------------------------------------------------------------------------
+struct StridedGemm {
+  int64_t M = 0, N = 0, K = 0, P = 0;
+  int64_t sam = 1, sak = 1, sap = 0;
+  int64_t sbk = 1, sbn = 1, sbp = 0;
+  int64_t scm = 1, scn = 1, scp = 0;
+  const int* kperm = nullptr;
+};
+cudaError_t launch_strided_gemm(const Ctx& c, const StridedGemm& g, const void* A,
+                                const void* B, void* C, const PgaScalars* scal,
+                                cudaStream_t st);
+cudaError_t launch_warm_scatter(const Ctx& c, int64_t n, int64_t P, const void* W,
+                                const int* perm, void* Q, const PgaScalars* scal,
+                                cudaStream_t st);
 
 // ----------------------------------------------------------------------------------
 // PGA bookkeeping kernels

@@ -550,6 +550,42 @@ jacobi_svt_cluster_kernel(const JArgs a) {
       if (c < n) permall[c] = dsm_ld(permp(c), 0);
     }
     __syncthreads();
+    if (a.io.W != nullptr) {
+      // warm-start basis (see write_basis): the n columns of nonzero norm in position
+      // order (columns moved during the sweeps; padding columns are exactly zero), each
+      // written by the CTA holding it; the identity when a column is (near) zero, not
+      // finite, or the sweeps did not converge
+      __shared__ int s_wok;
+      if (threadIdx.x == 0) {
+        int cnt = 0, ok = !rotated;
+        for (int c = 0; c < np; ++c) {
+          const T v = gval[c];
+          if (isfinite(v) && v > basis_min_norm2<T>()) {
+            if (cnt < n) list[cnt] = c;
+            ++cnt;
+          } else if (v != T(0)) {
+            ok = 0;
+          }
+        }
+        s_wok = ok && cnt == n;
+      }
+      __syncthreads();
+      const bool wok = s_wok != 0;
+      T* Wo = reinterpret_cast<T*>(a.io.W) + (size_t)slice * n * n;
+      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int r = idx % n, oc = idx / n;
+        if (wok) {
+          const int pos = list[oc];
+          if (pos % C == rank) Wo[idx] = Wl[r + (size_t)ld * (pos / C)] / sqrt(gval[pos]);
+        } else if (rank == 0) {
+          Wo[idx] = r == oc ? T(1) : T(0);
+        }
+      }
+      if (rank == 0)
+        for (int r = threadIdx.x; r < n; r += blockDim.x)
+          a.io.Wperm[(size_t)slice * n + r] = wok ? permall[r] : r;
+      __syncthreads();
+    }
     if (threadIdx.x == 0) {
       int st = 0, k = 0;
       T nuc = T(0);

@@ -139,6 +139,43 @@ __device__ __forceinline__ bool rotate_regs(T (&x)[E], T (&y)[E], T& nx, T& ny, 
   return true;
 }
 
+// Squared column norm below which a converged column is not normalised into the basis
+// of a warm start (the working matrix is scaled so that its largest entry lies in
+// [1, 2), so these are far below any singular value that matters).
+template <typename T> __device__ __forceinline__ T basis_min_norm2();
+template <> __device__ __forceinline__ double basis_min_norm2<double>() { return 1e-280; }
+template <> __device__ __forceinline__ float basis_min_norm2<float>() { return 1e-30f; }
+
+// Warm-start output of the SVT kernels: the n x n orthonormal basis of the side the
+// kernel orthogonalised, Wb(r, c) = Z(r, c) / ||z_c|| (rows in the QR order, Z the
+// rotated R^T held as columns of leading dimension ld, z_c its columns 0..n-1) and the
+// QR permutation.  A slice that did not converge or has a column of (near) zero norm
+// gets the identity and the identity permutation, so that the caller's basis stays
+// orthogonal.  Called by every thread of the CTA (contains a barrier).
+template <typename T>
+__device__ void write_basis(const JacobiIO& io, int64_t slice, int n, int ld, const T* Z,
+                            const T* nrm2, const int* perm, bool not_converged) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    int ok = !not_converged;
+    for (int c = 0; c < n && ok; ++c) {
+      const T v = nrm2[c];
+      ok = isfinite(v) && v > basis_min_norm2<T>();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  const bool ok = s_ok != 0;
+  T* Wo = reinterpret_cast<T*>(io.W) + (size_t)slice * n * n;
+  int* Po = io.Wperm + (size_t)slice * n;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx % n, c = idx / n;
+    Wo[idx] = ok ? Z[r + (size_t)ld * c] / sqrt(nrm2[c]) : (r == c ? T(1) : T(0));
+  }
+  for (int r = threadIdx.x; r < n; r += blockDim.x) Po[r] = ok ? perm[r] : r;
+  __syncthreads();
+}
+
 // Round-robin pairing on n (even) items: item n-1 fixed, the others on a circle.
 __host__ __device__ constexpr int rr_i(int r, int k, int n) {
   return k == 0 ? n - 1 : (r + k) % (n - 1);
@@ -636,6 +673,7 @@ jacobi_svt_kernel(const JArgs a) {
     column_norms();
     if (nrot) atomicAdd(&s_rot, nrot);
     __syncthreads();
+    if (a.io.W != nullptr) write_basis(a.io, slice, n, ld, W, nrm2, perm, rotated);
     if (a.io.phases && threadIdx.x == 0) tph[3] = clock64();
 
     // ---- 3. shrink (or truncate, or report sigma) and reconstruct
