@@ -1295,7 +1295,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "mixed"])
     ap.add_argument("--tc-tile-n", type=int, default=0, choices=[0, 32, 64, 128, 256],
                     help="LT_MIXED tensor-core tile width (0: the library's choice)")
-    ap.add_argument("--jacobi-pairwise", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--jacobi-pairwise", type=int, default=0, choices=[0, 1, 2, 3],
                     help="1: rotate column pairs straight through shared memory (no "
                          "register blocks)")
     ap.add_argument("--jacobi-cluster", type=int, default=0, choices=[0, 1, 3, 4],

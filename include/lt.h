@@ -103,10 +103,13 @@ typedef enum {
                                 default) lets the planner choose from min(I1, I2) */
   LT_OPT_JACOBI_BLOCK = 5,   /* SVT kernel: 1 = rotate column pairs straight through
                                 shared memory; 0 (default) = FP32 contexts hold blocks of
-                                2-4 columns per group in registers where they fit; 2 =
+                                2 columns per group in registers where they fit (for
+                                n <= 144 the wide form of value 3); 2 =
                                 FP32 register blocks with the group width forced by
                                 LT_OPT_JACOBI_GROUP (8: blocks of 2, n <= 144; 16: blocks
-                                of 4 (n <= 144) or 2; 32: blocks of 2) */
+                                of 4 (n <= 144) or 2; 32: blocks of 2); 3 = FP32 wide
+                                form for n <= 144: 16-lane groups with blocks of 2, one
+                                group per block pair of a round (up to 576 threads) */
   LT_OPT_TC_MODE_MIN = 6,    /* LT_MIXED: a mode k >= 4 with I_k >= this value (default
                                 64; modes above 224 never) is applied in a pass of its own
                                 on the tensor cores; mode 3 and smaller modes are applied
@@ -139,7 +142,15 @@ typedef enum {
                                 other roles' first waits expire after LT_OPT_TC_WAIT_US
                                 and every call that reaches the kernel reports
                                 LT_DEV_TIMEOUT with undefined output; 0 (default) = off */
-  LT_OPT_WARM_START = 13     /* lt_pga_complete (real transforms): 0 (default) = every
+  LT_OPT_AUTOTUNE = 14,      /* lt_pga_complete and lt_pga_complete_batched (real
+                                transforms): 1 = the first call on a slice shape the
+                                context was not tuned for times the SVT kernel forms
+                                (lt_autotune_svt) on that problem's first-iterate input
+                                step * obs at the threshold step * tau and keeps the
+                                fastest; the batched call tunes each slice shape once and
+                                gives its other contexts of that shape the same forms.
+                                Such a call synchronises the stream.  0 (default) = off */
+  LT_OPT_WARM_START = 13,    /* lt_pga_complete (real transforms): 0 (default) = every
                                 iteration's SVT starts from scratch; p >= 2 = warm start
                                 with period p.  Iteration j of a call (j = 0, 1, ...) with
                                 j % p == 0 thresholds L(G)^p from scratch and keeps the

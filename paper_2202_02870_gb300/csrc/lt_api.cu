@@ -498,7 +498,7 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
       c->profile = value != 0.0;
       return LT_OK;
     case LT_OPT_JACOBI_BLOCK:
-      if (!(value == 0 || value == 1 || value == 2)) return LT_ERR_ARG;
+      if (!(value == 0 || value == 1 || value == 2 || value == 3)) return LT_ERR_ARG;
       c->jacobi_pairwise = (int)value;
       return LT_OK;
     case LT_OPT_JACOBI_CLUSTER:
@@ -520,6 +520,10 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
     case LT_OPT_NU:
       if (!(value > 0.0 && value <= 1.0)) return LT_ERR_ARG;
       c->nu = value;
+      return LT_OK;
+    case LT_OPT_AUTOTUNE:
+      if (!(value == 0 || value == 1)) return LT_ERR_ARG;
+      c->autotune = (int)value;
       return LT_OK;
     case LT_OPT_WARM_START:
       if (!(value == 0 || (value >= 2 && value <= 1e6)) || value != std::floor(value))
@@ -1041,6 +1045,24 @@ cudaError_t pga_end(PgaRun& r, lt_pga_state* state, lt_pga_report* report, cudaS
   return e;
 }
 
+// LT_OPT_AUTOTUNE: the SVT kernel forms are timed (lt_autotune_svt) on the first
+// iterate's thresholding input, step * obs (X^0 = 0 makes G = step P_Omega(M)), at the
+// threshold step * tau, with the run's G_hat region as output and its Jacobi region as
+// workspace (forms needing more are skipped); the fastest stays set on the context, which
+// remembers the slice shape.  Synchronises the stream.  The run is then re-planned (the
+// chosen form needs no more workspace than the region it was timed in).
+lt_status pga_autotune(lt_ctx h, PgaRun& r, const uint8_t* mask, const void* obs, double tau,
+                       double step, void* X, void* ws, size_t ws_bytes, cudaStream_t st) {
+  Ctx& c = *r.c;
+  lt_tune_report rep;
+  const lt_status s = lt_autotune_svt(h, r.I1, r.I2, obs, step * tau, r.Gh, r.io.scratch,
+                                      align256(r.L.jp.ws_bytes), st, &rep);
+  if (s == LT_ERR_CUDA) return s;  // otherwise (no form fitted) the options stay as they were
+  c.tuned_I1 = r.I1;
+  c.tuned_I2 = r.I2;
+  return pga_prepare(c, r.I1, r.I2, mask, obs, tau, step, X, ws, ws_bytes, &r);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1058,6 +1080,9 @@ lt_status lt_pga_complete(lt_ctx ctx, int64_t I1, int64_t I2, const uint8_t* mas
   lt_status s = pga_prepare(c, I1, I2, mask, obs, tau, step, X, ws, ws_bytes, &r);
   if (s != LT_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
+  if (c.autotune && !c.fourier_n && (c.tuned_I1 != I1 || c.tuned_I2 != I2) &&
+      (s = pga_autotune(ctx, r, mask, obs, tau, step, X, ws, ws_bytes, st)) != LT_OK)
+    return s;
   cudaError_t e = pga_begin(r, state, tol, st);
   const int64_t k0 = (state && state->k > 0) ? state->k : 0;
   for (int64_t j = 0; j < iters && e == cudaSuccess; ++j) {
@@ -1119,6 +1144,36 @@ lt_status lt_pga_complete_batched(int nprob, const lt_ctx* ctxs, const int64_t* 
   }
   cudaStream_t st = (cudaStream_t)stream;
   Ctx& c0 = *reinterpret_cast<Ctx*>(ctxs[0]);
+  // LT_OPT_AUTOTUNE: once per slice shape in the batch; contexts of a shape tuned here
+  // take the same forms
+  off = 0;
+  for (int i = 0; i < nprob; ++i) {
+    Ctx& ci = *reinterpret_cast<Ctx*>(ctxs[i]);
+    size_t b = 0;
+    lt_workspace_size(ctxs[i], LT_OP_PGA, I1[i], I2[i], 0, &b);
+    if (ci.autotune && !ci.fourier_n && (ci.tuned_I1 != I1[i] || ci.tuned_I2 != I2[i])) {
+      int from = -1;
+      for (int j = 0; j < i && from < 0; ++j) {
+        const Ctx& cj = *reinterpret_cast<Ctx*>(ctxs[j]);
+        if (I1[j] == I1[i] && I2[j] == I2[i] && cj.tuned_I1 == I1[i] && cj.tuned_I2 == I2[i])
+          from = j;
+      }
+      if (from >= 0) {
+        const Ctx& cj = *reinterpret_cast<Ctx*>(ctxs[from]);
+        ci.jacobi_group = cj.jacobi_group;
+        ci.jacobi_pairwise = cj.jacobi_pairwise;
+        ci.tuned_I1 = I1[i];
+        ci.tuned_I2 = I2[i];
+        s = pga_prepare(ci, I1[i], I2[i], mask[i], obs[i], tau[i], step[i], X[i], w + off,
+                        align256(b), &runs[i]);
+      } else {
+        s = pga_autotune(ctxs[i], runs[i], mask[i], obs[i], tau[i], step[i], X[i], w + off,
+                         align256(b), st);
+      }
+      if (s != LT_OK) return s;
+    }
+    off += align256(b);
+  }
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < nprob && e == cudaSuccess; ++i) e = pga_begin(runs[i], nullptr, 0.0, st);
 
@@ -1215,7 +1270,7 @@ lt_status lt_autotune_svt(lt_ctx ctx, int64_t I1, int64_t I2, const void* A, dou
   const int keep_g = c.jacobi_group, keep_b = c.jacobi_pairwise;
   struct Form { int g, b; };
   std::vector<Form> forms = {{0, 0}, {8, 1}, {16, 1}, {32, 1}};
-  if (c.elem == 4) forms.insert(forms.end(), {{8, 2}, {16, 2}, {32, 2}});
+  if (c.elem == 4) forms.insert(forms.end(), {{8, 2}, {16, 2}, {32, 2}, {16, 3}});
   double best = INFINITY, dflt = INFINITY;
   Form pick = {keep_g, keep_b};
   int timed = 0;

@@ -129,10 +129,12 @@ struct JArgs {
 constexpr int kMaxThreadsF32 = 768;
 constexpr int kMaxThreadsF64 = 576;
 constexpr int kMaxThreadsBlocked = 512;  // register-blocked FP32 sweeps: 128 registers
+constexpr int kMaxThreadsBlockedWide = 576;  // wide form: 36 groups of 16, 113 registers
 cudaError_t launch_svt_f32_blk_a(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_blk_b(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_blk_c(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_blk_d(const JArgs& a, int grid, cudaStream_t st);
+cudaError_t launch_svt_f32_blk_e(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_pw_a(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f32_pw_b(const JArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_svt_f64_a(const JArgs& a, int grid, cudaStream_t st);

@@ -257,6 +257,24 @@ def test_svt_forced_register_blocks(group, shape):
     assert lt.lt_last_device_status(ctx) == 0
 
 
+@pytest.mark.parametrize("shape", [(37, 23), (100, 130), (144, 176), (176, 144), (17, 3)])
+def test_svt_wide_register_blocks(shape):
+    """FP32 wide form (LT_OPT_JACOBI_BLOCK = 3: 16-lane groups with blocks of 2, one group
+    per block pair of a round, up to 576 threads) against the oracle, on shapes with
+    npad padded (37, 23 and 17, 3), 7 and 9 rows per lane, both orientations."""
+    rng = np.random.default_rng(shape[0] * 3 + shape[1])
+    transforms = [("dct", 3)]
+    full = tuple(shape) + (3,)
+    A = rng.standard_normal(full)
+    ctx = make_ctx(transforms, lt.LT_FP32)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_JACOBI_BLOCK, 3)
+    D = empty_dev(full, torch.float32)
+    lt.lt_svt(ctx, to_dev(A, torch.float32), 1.0, D)
+    torch.cuda.synchronize()
+    assert rel(from_dev(D, full), O.svt(A, 1.0, oracle_mats(transforms))) <= TOL[lt.LT_FP32]
+    assert lt.lt_last_device_status(ctx) == 0
+
+
 @pytest.mark.parametrize("prec,scale", [(lt.LT_FP64, 1e-150), (lt.LT_FP64, 1e-30),
                                         (lt.LT_FP64, 1e30), (lt.LT_FP64, 1e150),
                                         (lt.LT_FP32, 1e-25), (lt.LT_FP32, 1e25)])

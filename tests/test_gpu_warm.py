@@ -166,3 +166,38 @@ def test_warm_ignored_by_the_batched_call():
     for (c, obs, _), Xb in zip(probs, Xs):
         cold, _, _ = run(c, obs, lt.LT_FP64, 6, 0)
         assert np.array_equal(from_dev(Xb, obs.shape), cold)
+
+
+@pytest.mark.parametrize("prec", [lt.LT_FP64, lt.LT_FP32])
+def test_autotune_option_single_and_batched(prec):
+    """LT_OPT_AUTOTUNE: the first PGA call on a new slice shape times the SVT kernel forms
+    on the problem's first-iterate input and keeps the fastest; the iterates stay within
+    the bound of the oracle (single call, a second call on the tuned context, and a batch
+    of three problems of two shapes, one tuning per shape)."""
+    probs = []
+    for i, (I1, I2) in enumerate(((24, 20), (20, 24), (24, 20))):
+        c = synth.completion_case(34, I1, I2, (3, 4), rank=3, rho=0.4, problem=i)
+        c.update(tau=0.3, step=1.0)
+        obs, Ms = inputs(c)
+        ref, _ = O.pga(c["mask"], obs, 0.3, 1.0, 8, Ms)
+        probs.append((c, obs, ref))
+    dt = dtype_of(prec)
+    c, obs, ref = probs[0]
+    ctx = make_ctx(c["transforms"], prec)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_AUTOTUNE, 1)
+    for _ in range(2):
+        X = to_dev(np.zeros(obs.shape), dt)
+        lt.lt_pga_complete(ctx, to_dev(c["mask"]), to_dev(obs, dt), 0.3, 1.0, 8, X)
+        torch.cuda.synchronize()
+        assert rel(from_dev(X, obs.shape), ref) <= TOL[prec]
+    ctxs = [make_ctx(p[0]["transforms"], prec) for p in probs]
+    for cx in ctxs:
+        lt.lt_ctx_set_option(cx, lt.LT_OPT_AUTOTUNE, 1)
+    Xs = [to_dev(np.zeros(p[1].shape), dt) for p in probs]
+    lt.lt_pga_complete_batched(ctxs, [to_dev(p[0]["mask"]) for p in probs],
+                               [to_dev(p[1], dt) for p in probs], [0.3] * 3, [1.0] * 3, 8, Xs)
+    torch.cuda.synchronize()
+    for (c, obs, ref), Xb in zip(probs, Xs):
+        assert rel(from_dev(Xb, obs.shape), ref) <= TOL[prec]
+    with pytest.raises(lt.LtError):
+        lt.lt_ctx_set_option(ctxs[0], lt.LT_OPT_AUTOTUNE, 2)
