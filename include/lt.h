@@ -142,6 +142,13 @@ typedef enum {
                                 other roles' first waits expire after LT_OPT_TC_WAIT_US
                                 and every call that reaches the kernel reports
                                 LT_DEV_TIMEOUT with undefined output; 0 (default) = off */
+  LT_OPT_TRANSFORM_TMA = 15, /* FP32 / LT_MIXED mode-product passes outside the PGA
+                                loop (lt_transform, lt_inverse, lt_product, lt_svt, ...):
+                                1 (default) = tiles move through the tensor memory
+                                accelerator (a ring of TMA loads, TMA stores) where the
+                                view allows it (16-byte aligned buffers, I1 I2 ... a
+                                multiple of 4, at most 256 slices per pass); 0 = the
+                                SIMT loads and stores.  The results are identical. */
   LT_OPT_AUTOTUNE = 14,      /* lt_pga_complete and lt_pga_complete_batched (real
                                 transforms): 1 = the first call on a slice shape the
                                 context was not tuned for times the SVT kernel forms

@@ -521,6 +521,10 @@ lt_status lt_ctx_set_option(lt_ctx ctx, lt_option opt, double value) {
       if (!(value > 0.0 && value <= 1.0)) return LT_ERR_ARG;
       c->nu = value;
       return LT_OK;
+    case LT_OPT_TRANSFORM_TMA:
+      if (!(value == 0 || value == 1)) return LT_ERR_ARG;
+      c->transform_tma = (int)value;
+      return LT_OK;
     case LT_OPT_AUTOTUNE:
       if (!(value == 0 || value == 1)) return LT_ERR_ARG;
       c->autotune = (int)value;

@@ -44,6 +44,7 @@ struct Ctx {
   int tc_tile_n = 0;                  // LT_MIXED: forced tensor-core tile width (0 = auto)
   double tc_wait_us = 0.0;            // LT_MIXED: tensor-core wait limit (0 = default 1 s)
   int tc_no_loads = 0;                // LT_MIXED test switch: no TMA copies are issued
+  int transform_tma = 1;              // FP32 passes without PGA fusions through TMA
   int autotune = 0;                   // PGA: time the SVT kernel forms on a new slice shape
   int64_t tuned_I1 = -1, tuned_I2 = -1;  // slice shape the forms were last tuned for
   int warm_period = 0;                // PGA warm start: 0 = off; p >= 2: iterations j with

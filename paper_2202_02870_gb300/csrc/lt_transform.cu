@@ -15,7 +15,10 @@
 //   FUSE_PGA_INVERSE  (last pass store)  X_new -> x_out; per-CTA partial sums of
 //                                          ||Y - X_new||^2, ||X_new||^2 and, if asked,
 //                                          ||mask (X_new - obs)||^2 (FP64 across tiles)
+#include <cuda.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "lt_internal.cuh"
 
@@ -61,15 +64,18 @@ struct PassArgs {
 // and two of the coefficients feed 32 FMAs.  Items are ordered output chunk first, so
 // the 8 x 4 threads of a warp mostly share j0 (uniform coefficient loads).  Returns the
 // buffer holding the result.
-template <int TS>
-__device__ __forceinline__ float* modes_f32(const TransformPass& p, const float* mats_s,
-                                            const int* moff_s, float* src, float* dst) {
-  constexpr int R = 8, C = 4;
+// One mode (index q of the pass) of the FP32 mode products of a tile, src -> dst; a work
+// item computes R consecutive outputs of a fibre for C = 4 columns (R = 8; R = 2 spreads
+// passes over few short fibres, e.g. a tile of 8 rows, over all warps).
+template <int TS, int R = 8>
+__device__ __forceinline__ void mode_f32(const TransformPass& p, int q, const float* mats_s,
+                                         const int* moff_s, const float* src, float* dst) {
+  constexpr int C = 4;
   const int Pg = (int)p.Pg;
   const int cg = threadIdx.x % (TS / C);
   const int rs = threadIdx.x / (TS / C);
   const int nrs = blockDim.x / (TS / C);
-  for (int q = 0; q < p.nm; ++q) {
+  {
     const int I = p.msize[q], st = p.mstride[q], Ip = padded_rows(I);
     const float* MT = mats_s + moff_s[q];
     const int nch = (I + R - 1) / R, nfib = Pg / I;
@@ -88,9 +94,17 @@ __device__ __forceinline__ float* modes_f32(const TransformPass& p, const float*
       const float* mp = MT + j0;
       for (int i = 0; i < I; ++i) {
         const float4 x = *reinterpret_cast<const float4*>(xp + (size_t)st * i * TS);
-        const float4 m0 = *reinterpret_cast<const float4*>(mp + i * Ip);
-        const float4 m1 = *reinterpret_cast<const float4*>(mp + i * Ip + 4);
-        const float mv[R] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
+        float mv[R];
+        if constexpr (R == 8) {
+          const float4 m0 = *reinterpret_cast<const float4*>(mp + i * Ip);
+          const float4 m1 = *reinterpret_cast<const float4*>(mp + i * Ip + 4);
+          mv[0] = m0.x; mv[1] = m0.y; mv[2] = m0.z; mv[3] = m0.w;
+          mv[4] = m1.x; mv[5] = m1.y; mv[6] = m1.z; mv[7] = m1.w;
+        } else {
+          static_assert(R == 2, "R is 8 or 2");
+          const float2 m0 = *reinterpret_cast<const float2*>(mp + i * Ip);
+          mv[0] = m0.x; mv[1] = m0.y;
+        }
         const float xv[C] = {x.x, x.y, x.z, x.w};
 #pragma unroll
         for (int r = 0; r < R; ++r)
@@ -103,6 +117,16 @@ __device__ __forceinline__ float* modes_f32(const TransformPass& p, const float*
           *reinterpret_cast<float4*>(dst + (size_t)(fbase + st * (j0 + r)) * TS + cg * C) =
               make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
     }
+  }
+}
+
+// All modes of the pass, ping-ponging between src and dst; returns the buffer holding
+// the result.
+template <int TS>
+__device__ __forceinline__ float* modes_f32(const TransformPass& p, const float* mats_s,
+                                            const int* moff_s, float* src, float* dst) {
+  for (int q = 0; q < p.nm; ++q) {
+    mode_f32<TS>(p, q, mats_s, moff_s, src, dst);
     __syncthreads();
     float* t = src; src = dst; dst = t;
   }
@@ -381,6 +405,177 @@ size_t smem_bytes(const TransformPass& p, int ts) {
   return ((sizeof(T) == 4 ? 3 : 2) * (size_t)p.Pg * ts + mats) * sizeof(T);
 }
 
+// ---------------------------------------------------------------------------------
+// Plain FP32 passes through the tensor memory accelerator.  The view [outer][Pg][Sg]
+// is a 2-D tensor of Pg * outer rows of Sg floats, and a tile (Pg rows x TS columns of
+// one outer block) is one TMA box: thread 0 keeps up to kTmaStages tiles in flight into a
+// ring of shared-memory stages (mbarrier complete_tx), every thread computes the mode
+// products of the current tile between its stage and one scratch buffer, and thread 0
+// writes the result back with one TMA store; once the store has read it, the stage takes
+// the load of a later tile.  Two CTAs share an SM (two tiles' mode products in flight).
+// The arithmetic is mode_f32's, so the results equal the SIMT pass bit for bit.  Every
+// wait on an mbarrier is bounded (1 s; then LT_DEV_TIMEOUT, the loop stops, the loads in
+// flight are drained with bounded waits and the stores completed before the CTA exits).
+// ---------------------------------------------------------------------------------
+constexpr int kTmaStages = 8;
+constexpr unsigned long long kTmaWaitNs = 1000000000ull;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool tma_mbar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity; false after kTmaWaitNs.
+__device__ bool tma_mbar_wait(uint32_t a, uint32_t parity) {
+  if (tma_mbar_try(a, parity)) return true;
+  unsigned long long t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (uint32_t i = 1;; ++i) {
+    if (tma_mbar_try(a, parity)) return true;
+    if ((i & 127u) == 0) {
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > kTmaWaitNs) return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                              int x, int y, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_tile(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(src)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+template <int TS, int R>
+__global__ void __launch_bounds__(kThreads, 2)
+transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
+                     const __grid_constant__ CUtensorMap map_out, const PassArgs a,
+                     int stages, int32_t* status) {
+  extern __shared__ __align__(16) unsigned char tma_smem[];
+  const TransformPass& p = a.p;
+  const int Pg = (int)p.Pg;
+  const uint32_t tile_bytes = (uint32_t)Pg * TS * 4;
+  const uint32_t tile_pad = (tile_bytes + 1023u) & ~1023u;
+  // [stages][T] tiles (1024-byte aligned), the matrices, the barriers
+  const uint32_t raw = smem_addr(tma_smem);
+  unsigned char* base = tma_smem + (((raw + 1023u) & ~1023u) - raw);
+  float* stage_buf = reinterpret_cast<float*>(base);
+  float* tbuf = reinterpret_cast<float*>(base + (size_t)stages * tile_pad);
+  float* mats_s = reinterpret_cast<float*>(base + (size_t)(stages + 1) * tile_pad);
+  int moff_s[kMaxModes];
+  int mat_elems = 0;
+  for (int q = 0; q < p.nm; ++q) {
+    moff_s[q] = mat_elems;
+    mat_elems += p.msize[q] * padded_rows(p.msize[q]);
+  }
+  uint64_t* bars = reinterpret_cast<uint64_t*>(mats_s + ((mat_elems + 1) & ~1));
+  __shared__ int s_ok;
+
+  // stage the matrices transposed with rows padded to a multiple of 8 (as transform_kernel)
+  for (int q = 0; q < p.nm; ++q) {
+    const float* src = reinterpret_cast<const float*>(a.mats) + p.mat_off[q];
+    const int I = p.msize[q], Ip = padded_rows(I);
+    for (int idx = threadIdx.x; idx < I * Ip; idx += blockDim.x) {
+      const int i = idx / Ip, j = idx % Ip;
+      mats_s[moff_s[q] + idx] = j < I ? src[j * I + i] : 0.f;
+    }
+  }
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + s)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+
+  // a CTA takes a contiguous run of tiles (consecutive column ranges of the same rows),
+  // so that every row of its tiles is read and written in long runs
+  const int64_t tpo = (p.Sg + TS - 1) / TS;
+  const int64_t ntiles = p.outer * tpo;
+  const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
+  const int64_t first = (int64_t)blockIdx.x * per;
+  const int64_t mine = first < ntiles ? std::min<int64_t>(per, ntiles - first) : 0;
+  auto coords = [&](int64_t i, int& x, int& y) {
+    const int64_t t = first + i;
+    x = (int)((t % tpo) * TS);
+    y = (int)((t / tpo) * Pg);
+  };
+  int64_t issued = 0;  // tiles whose load thread 0 has issued
+  if (threadIdx.x == 0)
+    for (; issued < stages && issued < mine; ++issued) {
+      int x, y;
+      coords(issued, x, y);
+      tma_load_tile(smem_addr(stage_buf) + (uint32_t)(issued % stages) * tile_pad, &map_in,
+                    smem_addr(bars + issued % stages), x, y, tile_bytes);
+    }
+  int64_t i = 0;
+  for (; i < mine; ++i) {
+    const int s = (int)(i % stages);
+    const bool ok = tma_mbar_wait(smem_addr(bars + s), (uint32_t)((i / stages) & 1));
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) atomicOr(status, LT_DEV_TIMEOUT);
+      break;
+    }
+    // an odd number of modes leaves the result in T: the store of the previous tile must
+    // have read it before T is written again
+    if ((p.nm & 1) && threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+    __syncthreads();
+    float* X = stage_buf + (size_t)s * (tile_pad / 4);
+    // modes in turn, stage -> T -> stage -> ...; the result is in T after an odd number
+    float* src = X;
+    float* dst = tbuf;
+    for (int q = 0; q < p.nm; ++q) {
+      mode_f32<TS, R>(p, q, mats_s, moff_s, src, dst);
+      __syncthreads();
+      float* t = src; src = dst; dst = t;
+    }
+    // generic-proxy writes of the result (and reads of the stage) before the async-proxy
+    // store and the next load into the stage
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int x, y;
+      coords(i, x, y);
+      tma_store_tile(&map_out, smem_addr(src), x, y);
+      // with the result in the stage, the stage takes its next load only after the store
+      // has read it (with the result in T the stage is free already)
+      if (!(p.nm & 1)) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      if (issued < mine) {
+        coords(issued, x, y);
+        tma_load_tile(smem_addr(stage_buf) + (uint32_t)s * tile_pad, &map_in,
+                      smem_addr(bars + s), x, y, tile_bytes);
+        ++issued;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    // after an expired wait, the loads still in flight (that tile's included) land before
+    // the CTA exits
+    for (int64_t j = i; j < issued; ++j)
+      tma_mbar_wait(smem_addr(bars + j % stages), (uint32_t)((j / stages) & 1));
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
+  __syncthreads();
+}
+
 template <typename T, int TS>
 cudaError_t launch_pass_t(const Ctx& c, const PassArgs& a, int grid, cudaStream_t st) {
   auto k = transform_kernel<T, TS>;
@@ -411,6 +606,96 @@ int occupancy(const TransformPass& p) {
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, transform_kernel<T, TS>, kThreads, p.smem) != cudaSuccess)
     nb = 1;
   return std::max(nb, 1);
+}
+
+// ---- TMA passes: host side
+using TmaEncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+TmaEncodeFn tma_encode_fn() {
+  static std::once_flag once;
+  static TmaEncodeFn fn = nullptr;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<TmaEncodeFn>(ptr);
+  });
+  return fn;
+}
+
+// The pass's view as a 2-D FP32 tensor: Pg * outer rows of Sg elements; box TS x Pg.
+bool tma_view(CUtensorMap* map, const void* ptr, const TransformPass& p, int ts) {
+  TmaEncodeFn fn = tma_encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)p.Sg, (cuuint64_t)(p.Pg * p.outer)};
+  const cuuint64_t strides[1] = {(cuuint64_t)p.Sg * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)ts, (cuuint32_t)p.Pg};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tile width of the TMA form of a pass (a box edge is at most 256 elements), or 0 when
+// the pass cannot take it.
+int tma_ts(const TransformPass& p) {
+  if (p.ts == 32 || p.ts == 128) return p.ts;
+  if (p.ts == 512) return 256;
+  return 0;
+}
+
+template <int TS, int R>
+cudaError_t launch_tma_t(const Ctx& c, const PassArgs& a, const CUtensorMap& mi,
+                         const CUtensorMap& mo, cudaStream_t st) {
+  const TransformPass& p = a.p;
+  const size_t tile_pad = ((size_t)p.Pg * TS * 4 + 1023) & ~size_t(1023);
+  size_t mats = 0;
+  for (int q = 0; q < p.nm; ++q) mats += (size_t)p.msize[q] * padded_rows(p.msize[q]) * 4;
+  mats = (mats + 15) & ~size_t(15);
+  // two CTAs per SM: half of the SM's shared memory each, less the per-CTA reservation
+  const size_t fixed = 1024 + tile_pad + mats;
+  const size_t limit = (size_t)kSmemOptin / 2 - 2048;
+  if (fixed + 2 * tile_pad + 8 * 2 > limit) return cudaErrorNotSupported;
+  int stages = (int)std::min<size_t>(kTmaStages, (limit - fixed) / (tile_pad + 8));
+  const size_t smem = fixed + (size_t)stages * tile_pad + 8 * (size_t)stages + 8;
+  auto k = transform_tma_kernel<TS, R>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = p.outer * ((p.Sg + TS - 1) / TS);
+  const int64_t grid = std::min<int64_t>(tiles, 2 * (int64_t)c.sms);
+  k<<<(unsigned)grid, kThreads, smem, st>>>(mi, mo, a, stages, c.d_status);
+  return cudaGetLastError();
+}
+
+// FP32 pass without a PGA fusion through TMA, or cudaErrorNotSupported when its view does
+// not meet the tensor-map rules (16-byte aligned base, Sg a multiple of 4, Pg <= 256).
+cudaError_t launch_pass_tma(const Ctx& c, const PassArgs& a, cudaStream_t st) {
+  const TransformPass& p = a.p;
+  const int ts = tma_ts(p);
+  if (ts == 0 || p.Pg > 256 || p.Sg % 4 != 0 || p.Sg > (int64_t)INT32_MAX ||
+      p.Pg * p.outer > (int64_t)INT32_MAX)
+    return cudaErrorNotSupported;
+  if ((reinterpret_cast<uintptr_t>(a.in) | reinterpret_cast<uintptr_t>(a.out)) & 15)
+    return cudaErrorNotSupported;
+  CUtensorMap mi, mo;
+  if (!tma_view(&mi, a.in, p, ts) || !tma_view(&mo, a.out, p, ts)) return cudaErrorNotSupported;
+  // work items of 8 outputs x 4 columns leave threads idle when the pass has fewer of
+  // them than the CTA has threads (a single mode over a tile of few rows): 2 outputs
+  int items = 1 << 30;
+  for (int q = 0; q < p.nm; ++q)
+    items = std::min<int>(items, (int)((p.Pg / p.msize[q]) * ((p.msize[q] + 7) / 8) * (ts / 4)));
+  const bool r2 = items < kThreads && p.nm == 1;
+  switch (ts) {
+    case 32: return r2 ? launch_tma_t<32, 2>(c, a, mi, mo, st) : launch_tma_t<32, 8>(c, a, mi, mo, st);
+    case 128: return r2 ? launch_tma_t<128, 2>(c, a, mi, mo, st) : launch_tma_t<128, 8>(c, a, mi, mo, st);
+    case 256: return r2 ? launch_tma_t<256, 2>(c, a, mi, mo, st) : launch_tma_t<256, 8>(c, a, mi, mo, st);
+  }
+  return cudaErrorNotSupported;
 }
 
 template <typename T>
@@ -557,6 +842,11 @@ cudaError_t launch_transform(const Ctx& c, const TransformPlan& plan, const void
         continue;
       }
       // unaligned buffers: the SIMT kernel applies the same mode product
+    }
+    if (c.elem == 4 && a.fuse_mode == FUSE_NONE && !a.p.tc && c.transform_tma) {
+      const cudaError_t e = launch_pass_tma(c, a, st);
+      if (e == cudaSuccess) continue;
+      if (e != cudaErrorNotSupported) return e;
     }
     const int grid = transform_grid(c, a.p);
     if (grid_out) *grid_out = grid;

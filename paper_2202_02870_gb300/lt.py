@@ -30,7 +30,7 @@ LT_FP64, LT_FP32, LT_MIXED = 0, 1, 2
 (LT_OPT_MAX_SWEEPS, LT_OPT_JACOBI_TOL, LT_OPT_OBJECTIVE, LT_OPT_PROFILE, LT_OPT_JACOBI_GROUP,
  LT_OPT_JACOBI_BLOCK, LT_OPT_TC_MODE_MIN, LT_OPT_TC_TILE_N, LT_OPT_MU0, LT_OPT_NU,
  LT_OPT_JACOBI_CLUSTER, LT_OPT_TC_WAIT_US, LT_OPT_TC_TEST_NO_LOADS, LT_OPT_WARM_START,
- LT_OPT_AUTOTUNE) = range(15)
+ LT_OPT_AUTOTUNE, LT_OPT_TRANSFORM_TMA) = range(16)
 LT_K_TRANSFORM, LT_K_JACOBI, LT_K_GEMM, LT_K_AUX = 0, 1, 2, 3
 KERNEL_FAMILIES = ("transform", "jacobi", "gemm", "aux")
 

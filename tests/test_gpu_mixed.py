@@ -233,3 +233,40 @@ def test_tc_bounded_wait_expires_then_context_recovers():
     assert lt.lt_last_device_status(ctx) == 0
     assert tc_launches(ctx) == 1
     assert rel(from_dev(Cd, (128, 64, 3)), O.product(A, B, oracle_mats(tr))) <= TOL
+
+
+# (I1, I2, trailing): a 256-slice pass of two modes plus a single-mode pass with wide tiles
+# (16, 16, 8), ragged tiles (Sg = 468), a single mode of 8, a view that is not a multiple
+# of 4 (SIMT fallback), and mode sizes 3 and 32 (one pass of 96 slices)
+TMA_SHAPES = [(24, 20, (16, 16, 8)), (36, 13, (16, 16)), (20, 10, (8,)), (33, 7, (5, 3)),
+              (64, 64, (3, 32))]
+
+
+@pytest.mark.parametrize("inplace", [False, True])
+@pytest.mark.parametrize("I1,I2,trailing", TMA_SHAPES)
+def test_transform_tma_equals_simt(I1, I2, trailing, inplace):
+    """FP32 transform and inverse passes through the tensor memory accelerator
+    (LT_OPT_TRANSFORM_TMA = 1, the default) give the same bits as the SIMT loads and
+    stores (0): the mode products are the same code; and both match the oracle."""
+    rng = np.random.default_rng(I1 * 5 + I2)
+    full = (I1, I2) + trailing
+    X = rng.uniform(-1, 1, full)
+    tr = [("dct", n) if k % 2 == 0 else ("matrix", synth.conditioned_matrix(rng, n, 10.0, True))
+          for k, n in enumerate(trailing)]
+    Ms = oracle_mats(tr)
+    outs = {}
+    for tma in (1, 0):
+        ctx = make_ctx(tr, lt.LT_FP32)
+        lt.lt_ctx_set_option(ctx, lt.LT_OPT_TRANSFORM_TMA, tma)
+        Xd = to_dev(X, torch.float32)
+        Y = Xd if inplace else empty_dev(full, torch.float32)
+        lt.lt_transform(ctx, Xd, Y)
+        Z = Y if inplace else empty_dev(full, torch.float32)
+        Yc = Y.clone()
+        lt.lt_inverse(ctx, Y, Z)
+        torch.cuda.synchronize()
+        assert lt.lt_last_device_status(ctx) == 0
+        outs[tma] = (Yc, Z.clone())
+    assert torch.equal(outs[1][0], outs[0][0]) and torch.equal(outs[1][1], outs[0][1])
+    assert rel(from_dev(outs[1][0], full), O.transform(X, Ms)) <= 1e-6
+    assert rel(from_dev(outs[1][1], full), X) <= 1e-5
