@@ -1055,6 +1055,13 @@ def run_pga5(args):
         prec = {"fp32": lt.LT_FP32, "mixed": lt.LT_MIXED}[name]
         ctx = lt.Context([3, 120], mats, prec)
         obs = obs64.float()
+        mu0 = 0.0
+        if args.mu0_frac > 0:
+            # continuation of Algorithm 5 with the paper's settings: mu_0 = nu ||M||_F,
+            # nu = 0.9, mu_bar = tau
+            mu0 = args.mu0_frac * float(torch.linalg.norm(obs64))
+            lt.lt_ctx_set_option(ctx, lt.LT_OPT_MU0, mu0)
+            lt.lt_ctx_set_option(ctx, lt.LT_OPT_NU, 0.9)
         X = torch.zeros(tshape, dtype=torch.float32, device=dev)
         wsb = torch.empty(lt.lt_workspace_size(ctx, lt.LT_OP_PGA, 540, 960), dtype=torch.uint8,
                           device=dev)
@@ -1069,6 +1076,7 @@ def run_pga5(args):
         ms = e0.elapsed_time(e1)
         out["to_residual"] = {
             "path": name, "tol": args.tol5, "max_iters": args.max_iters5,
+            "continuation": {"mu0": mu0, "nu": 0.9} if mu0 > 0 else None,
             "iters_done": rep.iters_done, "rel_residual": rep.rel_residual,
             "reached": bool(rep.rel_residual <= args.tol5), "device_status": rep.device_status,
             "seconds": round(ms / 1e3, 3), "ms_per_iter": round(ms / max(rep.iters_done, 1), 2),
@@ -1285,6 +1293,8 @@ def main():
     ap.add_argument("--tol5", type=float, default=0.0,
                     help="--case pga5: also run --precision (fp32 or mixed) from a cold "
                          "start until the relative residual is <= this value")
+    ap.add_argument("--mu0-frac", type=float, default=0.0,
+                    help="--case pga5 --tol5: continuation with mu_0 = this x ||M||_F, nu = 0.9")
     ap.add_argument("--max-iters5", type=int, default=300,
                     help="--case pga5: iteration cap of the --tol5 run")
     ap.add_argument("--case", default="pga",

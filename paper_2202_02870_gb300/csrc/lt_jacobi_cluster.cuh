@@ -131,7 +131,12 @@ jacobi_svt_cluster_kernel(const JArgs a) {
   const int ncl = gridDim.x / C;
   const int nvalid = n > rank ? (n - rank + C - 1) / C : 0;  // local columns with c < n
 
+  // phase boundaries (thread 0 of CTA 0 of the cluster, profiling only): slice start,
+  // QR start, sweeps start, sweeps end, selection end, coefficients end, rows end
+  const bool prof = a.io.phases != nullptr && rank == 0 && threadIdx.x == 0;
+  long long tph[7];
   for (int64_t slice = blockIdx.x / C; slice < jp.P; slice += ncl) {
+    if (prof) tph[0] = clock64();
     const T* A = Ain + slice * I1 * I2;
     T* D = a.io.D ? reinterpret_cast<T*>(a.io.D) + slice * I1 * I2 : nullptr;
     // ---- load the local columns of B (zero padding), local maximum
@@ -169,6 +174,7 @@ jacobi_svt_cluster_kernel(const JArgs a) {
     const T tau = T(a.io.tau) * sc;
     __syncthreads();
 
+    if (prof) tph[1] = clock64();
     // ---- 1. QR with column pivoting on the distributed columns
     for (int q = warp; q < nl; q += nwarps) {
       const T* col = Wl + (size_t)ld * q;
@@ -313,6 +319,7 @@ jacobi_svt_cluster_kernel(const JArgs a) {
     for (int q = threadIdx.x; q < nl; q += blockDim.x) { dsc[q] = T(1); isc[q] = T(1); }
     __syncthreads();
 
+    if (prof) tph[2] = clock64();
     // ---- 2. one-sided Jacobi on Z, pairs spread over the cluster
     auto column_norms = [&]() {
       for (int q0 = 0; q0 < nl; q0 += ngrp) {
@@ -541,6 +548,7 @@ jacobi_svt_cluster_kernel(const JArgs a) {
     }
     cl.sync();
 
+    if (prof) tph[3] = clock64();
     // ---- 3. shrink and reconstruct: every CTA copies the norms and the permutation of
     // all columns, builds the same list of kept columns, then computes its rows
     // columns moved between CTAs in the sweeps: scan every padded position (a zero
@@ -600,6 +608,7 @@ jacobi_svt_cluster_kernel(const JArgs a) {
         }
       }
       s_count = k;
+      if (prof) tph[4] = clock64();
       if (rank == 0) {
         if (st) atomicOr(a.status, st);
         if (a.io.info) {
@@ -621,6 +630,7 @@ jacobi_svt_cluster_kernel(const JArgs a) {
     }
     __syncthreads();
     const int k = s_count;
+    if (prof) tph[5] = clock64();
     for (int q = threadIdx.x; q < k; q += blockDim.x) {
       const int c = list[q];
       const T sg = sqrt(gval[c]);
@@ -680,6 +690,10 @@ jacobi_svt_cluster_kernel(const JArgs a) {
           else D[r + I1 * pc] = out[e];
         }
       }
+    }
+    if (prof) {
+      tph[6] = clock64();
+      for (int q = 0; q < 6; ++q) atomicAdd(a.io.phases + q, double(tph[q + 1] - tph[q]));
     }
     // no CTA may reload or leave while another still reads its columns
     cl.sync();
