@@ -589,11 +589,11 @@ lt_status plan_jacobi(const Ctx& c, int mode, int64_t I1, int64_t I2, JacobiPlan
     jp.E = E;
     if (B > 1) jp.npad = (jp.n + 2 * B - 1) / (2 * B) * (2 * B);
     jp.ld = std::max(jp.m, 32 * ((G * E + 31) / 32)) | 1;
-    if (c.elem == 4 && G == 16 && B == 2 && E <= 9) {
-      // wide FP32 form: the two groups of a warp hold blocks whose columns are two apart;
-      // with ld = 8 (mod 16) floats 2 ld = 16 (mod 32), so their 16-row accesses fall on
-      // the two opposite halves of the 32 banks (with an odd ld a third of the shared
-      // wavefronts were bank conflicts)
+    if (c.elem == 4 && B > 1) {
+      // FP32 block forms: a lane loads pairs of adjacent rows with 8-byte accesses, so
+      // ld must be even; ld = 8 (mod 16) floats also puts columns two apart (the two
+      // groups of a warp in the wide form) on opposite halves of the 32 banks (with an
+      // odd ld and one row per access a third of the shared wavefronts were conflicts)
       const int base = std::max(jp.m, 32 * ((G * E + 31) / 32));
       jp.ld = base + ((8 - base % 16) + 16) % 16;
     }

@@ -102,12 +102,93 @@ __device__ __forceinline__ void rotation_scaled(double al, double be, double g, 
   ic = x * y;
 }
 
-template <int G, typename T, int E>
-__device__ __forceinline__ T group_dot(const T (&x)[E], const T (&y)[E]) {
+// Packed pairs of FP32 values and the two-wide FMA of sm_100-class GPUs; each lane is
+// rounded as fmaf rounds it.
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float pk_sum(unsigned long long v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return lo + hi;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// A column of a block held in registers by a group of G lanes, E rows per lane: lane gl
+// holds rows gl + G e.  The FP32 form holds pairs of adjacent rows instead (rows
+// 2 gl + 2 G k and the next, k < E / 2, plus row 2 G (E / 2) + gl for odd E), so that one
+// 8-byte load fills a register pair and the dot products and rotations run as two-wide
+// FMAs; both forms cover rows 0 .. G E - 1.
+template <typename T, int G, int E>
+struct RegCol {
+  T v[E];
+  __device__ __forceinline__ void load(const T* col, int gl, bool active) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = active ? col[gl + G * e] : T(0);
+  }
+  __device__ __forceinline__ void store(T* col, int gl) const {
+#pragma unroll
+    for (int e = 0; e < E; ++e) col[gl + G * e] = v[e];
+  }
+};
+template <int G, int E>
+struct RegCol<float, G, E> {
+  static constexpr int EP = E / 2;
+  static constexpr bool kTail = (E % 2) != 0;
+  unsigned long long p[EP];
+  float t;
+  __device__ __forceinline__ void load(const float* col, int gl, bool active) {
+#pragma unroll
+    for (int k = 0; k < EP; ++k)
+      p[k] = active ? *reinterpret_cast<const unsigned long long*>(col + 2 * gl + 2 * G * k)
+                    : 0ULL;
+    t = (kTail && active) ? col[2 * G * EP + gl] : 0.f;
+  }
+  __device__ __forceinline__ void store(float* col, int gl) const {
+#pragma unroll
+    for (int k = 0; k < EP; ++k)
+      *reinterpret_cast<unsigned long long*>(col + 2 * gl + 2 * G * k) = p[k];
+    if (kTail) col[2 * G * EP + gl] = t;
+  }
+};
+
+// This lane's part of x . y
+template <typename T, int G, int E>
+__device__ __forceinline__ T reg_dot(const RegCol<T, G, E>& x, const RegCol<T, G, E>& y) {
   T g = T(0);
 #pragma unroll
-  for (int e = 0; e < E; ++e) g = fma(x[e], y[e], g);
+  for (int e = 0; e < E; ++e) g = fma(x.v[e], y.v[e], g);
   return g;
+}
+template <int G, int E>
+__device__ __forceinline__ float reg_dot(const RegCol<float, G, E>& x,
+                                         const RegCol<float, G, E>& y) {
+  unsigned long long a = 0ULL;
+#pragma unroll
+  for (int k = 0; k < RegCol<float, G, E>::EP; ++k) a = fma2(x.p[k], y.p[k], a);
+  float g = pk_sum(a);
+  if (RegCol<float, G, E>::kTail) g = fmaf(x.t, y.t, g);
+  return g;
+}
+
+// Pivot key of column c with squared norm s >= 0: the high 32 bits of s (an ordering of
+// the non-negative values) above the inverted index, so that the largest key is the
+// largest norm and, among equal keys, the smallest index.
+__device__ __forceinline__ unsigned long long pivot_key(double s, int c) {
+  return ((unsigned long long)__double_as_longlong(s) >> 32 << 32) | (0xffffffffu - (unsigned)c);
+}
+__device__ __forceinline__ unsigned long long pivot_key(float s, int c) {
+  return ((unsigned long long)__float_as_uint(s) << 32) | (0xffffffffu - (unsigned)c);
+}
+__device__ __forceinline__ int pivot_index(unsigned long long key) {
+  return (int)(0xffffffffu - (unsigned)(key & 0xffffffffULL));
 }
 
 // Rotate the register-held columns x, y (E rows per lane) given gamma = x.y over the
@@ -133,6 +214,37 @@ __device__ __forceinline__ bool rotate_regs(T (&x)[E], T (&y)[E], T& nx, T& ny, 
       x[e] = fma(cs, xe, -sn * ye);
       y[e] = fma(sn, xe, cs * ye);
     }
+  }
+  nx = nx - t * g;
+  ny = ny + t * g;
+  return true;
+}
+
+// rotate_regs on register columns; the FP32 form applies the same per-row FMAs two rows
+// at a time
+template <typename T, int G, int E>
+__device__ __forceinline__ bool reg_rotate(RegCol<T, G, E>& x, RegCol<T, G, E>& y, T& nx, T& ny,
+                                           T g, T tol2) {
+  return rotate_regs(x.v, y.v, nx, ny, g, tol2);
+}
+template <int G, int E>
+__device__ __forceinline__ bool reg_rotate(RegCol<float, G, E>& x, RegCol<float, G, E>& y,
+                                           float& nx, float& ny, float g, float tol2) {
+  if (!(nx > 0.f && ny > 0.f && g * g > tol2 * nx * ny)) return false;
+  float cs, sn, t;
+  rotation_fast(nx, ny, g, cs, sn, t);
+  const float h = sn / (1.f + cs);
+  const unsigned long long H = pk2(h, h), NH = pk2(-h, -h), S = pk2(sn, sn), NS = pk2(-sn, -sn);
+#pragma unroll
+  for (int k = 0; k < RegCol<float, G, E>::EP; ++k) {
+    const unsigned long long xe = x.p[k], ye = y.p[k];
+    x.p[k] = fma2(NS, fma2(H, xe, ye), xe);
+    y.p[k] = fma2(S, fma2(NH, ye, xe), ye);
+  }
+  if (RegCol<float, G, E>::kTail) {
+    const float xe = x.t, ye = y.t;
+    x.t = fmaf(-sn, fmaf(h, xe, ye), xe);
+    y.t = fmaf(sn, fmaf(-h, ye, xe), ye);
   }
   nx = nx - t * g;
   ny = ny + t * g;
@@ -216,7 +328,8 @@ jacobi_svt_kernel(const JArgs a) {
     dsc = reinterpret_cast<T*>(sp); sp += sizeof(T) * np;
     isc = reinterpret_cast<T*>(sp); sp += sizeof(T) * np;
   }
-  __shared__ int s_piv, s_count, s_rot;
+  __shared__ int s_count, s_rot;
+  __shared__ unsigned long long s_key[2];  // pivot keys of the QR steps, by parity
   // FP64 scaled sweeps: per-pair scalars of one batch of pairs (dot product; update
   // coefficients; rescale factors; rotate or not), so that the rotation parameters are
   // computed once per pair by one thread instead of on every lane of the pair's group
@@ -224,7 +337,6 @@ jacobi_svt_kernel(const JArgs a) {
   __shared__ T s_pg[kPairs], s_pa[kPairs], s_pb[kPairs], s_sx[kPairs], s_sy[kPairs];
   __shared__ int s_pr[kPairs];
   __shared__ unsigned long long s_maxbits;
-  __shared__ T s_alpha, s_beta, s_v0;
 
   const T* Ain = reinterpret_cast<const T*>(a.io.A);
   T* W = jp.w_in_smem ? Ws
@@ -281,65 +393,61 @@ jacobi_svt_kernel(const JArgs a) {
     __syncthreads();
 
     if (a.io.phases && threadIdx.x == 0) tph[1] = clock64();
-    // ---- 1. QR with column pivoting: B P = Q R (R in the upper triangle)
+    // ---- 1. QR with column pivoting: B P = Q R (R in the upper triangle).  The norms of
+    // the remaining columns are recomputed exactly by the trailing update of each step
+    // (rows j+1.. of the updated columns; no downdating), and the next pivot is the
+    // maximum of the keys (norm bits, inverted index) that the updating lanes post to
+    // shared memory, so that every thread finds the pivot and the Householder vector
+    // itself: two barriers per step.
+    if (threadIdx.x == 0) { s_key[0] = 0ULL; s_key[1] = 0ULL; }
+    __syncthreads();
     for (int c = warp; c < n; c += nwarps) {
       const T* col = W + (size_t)ld * c;
       T s = T(0);
       for (int r = lane; r < m; r += 32) s = fma(col[r], col[r], s);
       s = warp_allsum(s);
-      if (lane == 0) { nrm2[c] = s; ref[c] = s; perm[c] = c; }
+      if (lane == 0) {
+        nrm2[c] = s;
+        perm[c] = c;
+        atomicMax(&s_key[0], pivot_key(s, c));
+      }
     }
     __syncthreads();
     const bool prof = a.io.phases != nullptr && threadIdx.x == 0;
     long long tq = prof ? clock64() : 0;
     if (prof) tqr[0] = tqr[1] = tqr[2] = tqr[3] = 0;
+    T alpha_prev = T(0);  // R(j-1, j-1), stored once every thread has read B(j-1, j-1)
     for (int j = 0; j < n; ++j) {
-      if (warp == 0) {  // pivot: the remaining column of largest norm
-        T best = T(-1);
-        int bi = j;
-        for (int c = j + lane; c < n; c += 32)
-          if (nrm2[c] > best) { best = nrm2[c]; bi = c; }
-        warp_argmax(best, bi);
-        if (lane == 0) s_piv = bi;
-      }
-      __syncthreads();
+      // pivot: the remaining column of largest norm (ties: the smaller index)
+      const int p = pivot_index(s_key[j & 1]);
+      const T s = nrm2[p];  // ||B(j:m, p)||^2
       if (prof) { const long long t = clock64(); tqr[0] += t - tq; tq = t; }
-      const int p = s_piv;
       if (p != j) {
         for (int r = threadIdx.x; r < m; r += blockDim.x) {
           const T t0 = W[r + (size_t)ld * j];
           W[r + (size_t)ld * j] = W[r + (size_t)ld * p];
           W[r + (size_t)ld * p] = t0;
         }
-        if (threadIdx.x == 0) {
-          T t1 = nrm2[j]; nrm2[j] = nrm2[p]; nrm2[p] = t1;
-          t1 = ref[j]; ref[j] = ref[p]; ref[p] = t1;
-          const int t2 = perm[j]; perm[j] = perm[p]; perm[p] = t2;
-        }
+      }
+      if (threadIdx.x == 0) {
+        if (j > 0) W[(j - 1) + (size_t)ld * (j - 1)] = alpha_prev;
+        if (p != j) { const int t2 = perm[j]; perm[j] = perm[p]; perm[p] = t2; }
+        s_key[(j + 1) & 1] = 0ULL;  // read last in step j - 1, before its second barrier
       }
       __syncthreads();
       if (prof) { const long long t = clock64(); tqr[1] += t - tq; tq = t; }
-      if (warp == 0) {  // Householder vector v = x - alpha e_1 of x = B(j:m, j)
-        const T* col = W + (size_t)ld * j;
-        T s = T(0);
-        for (int r = j + lane; r < m; r += 32) s = fma(col[r], col[r], s);
-        s = warp_allsum(s);
-        if (lane == 0) {
-          const T x0 = col[j];
-          const T nx = sqrt(s);
-          const T alpha = (x0 >= T(0)) ? -nx : nx;
-          s_alpha = alpha;
-          s_v0 = x0 - alpha;
-          // beta = 2 / (v.v) = 1 / (alpha (alpha - x0)) = 1 / (||x|| (||x|| + |x0|))
-          s_beta = (s > T(0)) ? T(1) / (nx * (nx + fabs(x0))) : T(0);
-        }
-      }
-      __syncthreads();
-      if (prof) { const long long t = clock64(); tqr[2] += t - tq; tq = t; }
-      const T alpha = s_alpha, beta = s_beta, v0 = s_v0;
+      // Householder vector v = x - alpha e_1 of x = B(j:m, j), on every thread
       const T* vj = W + (size_t)ld * j;
+      const T x0 = vj[j];
+      const T nx = sqrt(s);
+      const T alpha = (x0 >= T(0)) ? -nx : nx;
+      const T v0 = x0 - alpha;
+      // beta = 2 / (v.v) = 1 / (alpha (alpha - x0)) = 1 / (||x|| (||x|| + |x0|))
+      const T beta = (s > T(0)) ? T(1) / (nx * (nx + fabs(x0))) : T(0);
+      if (prof) { const long long t = clock64(); tqr[2] += t - tq; tq = t; }
       // B(j:m, c) -= beta v (v . B(j:m, c)) for c > j; a warp takes four columns at a
-      // time so that four dot products and reductions are in flight together
+      // time so that four dot products and reductions are in flight together, and sums
+      // the squares of rows j+1.. of the updated columns (the next step's norms)
       for (int c0 = j + 1 + 4 * warp; c0 < n; c0 += 4 * nwarps) {
         T* col[4];
         T w[4];
@@ -358,43 +466,32 @@ jacobi_svt_kernel(const JArgs a) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) w[u] *= beta;
         __syncwarp();
+        T sq[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
+          sq[u] = T(0);
           if (c0 + u >= n) continue;  // uniform over the warp
           T* cu = col[u];
           if (lane == 0) cu[j] = fma(-w[u], v0, cu[j]);
-          for (int r = j + 1 + lane; r < m; r += 32) cu[r] = fma(-w[u], vj[r], cu[r]);
-        }
-        __syncwarp();
-        // downdate the remaining norms, lane u for column c0 + u; a column whose norm
-        // cancellation has eaten is recomputed by the whole warp
-        bool redo = false;
-        T nn = T(0);
-        if (lane < 4 && c0 + lane < n) {
-          const int c = c0 + lane;
-          const T rjc = W[j + (size_t)ld * c];
-          nn = nrm2[c] - rjc * rjc;
-          redo = nn <= T(0.01) * ref[c];
-          if (!redo) nrm2[c] = nn > T(0) ? nn : T(0);
-        }
-        unsigned mask = __ballot_sync(0xffffffffu, redo);
-        while (mask) {  // rare
-          const int u = __ffs(mask) - 1;
-          mask &= mask - 1;
-          const T* cu = col[u];
-          T sq = T(0);
-          for (int r = j + 1 + lane; r < m; r += 32) sq = fma(cu[r], cu[r], sq);
-          sq = warp_allsum(sq);
-          if (lane == 0) {
-            ref[c0 + u] = sq;
-            nrm2[c0 + u] = sq > T(0) ? sq : T(0);
+          for (int r = j + 1 + lane; r < m; r += 32) {
+            const T v = fma(-w[u], vj[r], cu[r]);
+            cu[r] = v;
+            sq[u] = fma(v, v, sq[u]);
           }
         }
+        warp_allsum4(sq);
+        if (lane < 4 && c0 + lane < n) {
+          const T q = lane == 0 ? sq[0] : lane == 1 ? sq[1] : lane == 2 ? sq[2] : sq[3];
+          nrm2[c0 + lane] = q;
+          atomicMax(&s_key[(j + 1) & 1], pivot_key(q, c0 + lane));
+        }
       }
-      if (threadIdx.x == 0) W[j + (size_t)ld * j] = alpha;
+      alpha_prev = alpha;
       __syncthreads();
       if (prof) { const long long t = clock64(); tqr[3] += t - tq; tq = t; }
     }
+    if (threadIdx.x == 0 && n > 0) W[(n - 1) + (size_t)ld * (n - 1)] = alpha_prev;
+    __syncthreads();
     // ---- Z = R^T (lower triangular), rows n.. zeroed
     for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
       const int r = idx % n, c = idx / n;
@@ -469,16 +566,12 @@ jacobi_svt_kernel(const JArgs a) {
                 if (by < 0) by += cfb;
               }
             }
-            T X[B][E], Y[B][E], nx[B], ny[B];
+            RegCol<T, G, E> X[B], Y[B];
+            T nx[B], ny[B];
 #pragma unroll
             for (int c = 0; c < B; ++c) {
-              const T* cx = W + (size_t)ld * (bx * B + c);
-              const T* cy = W + (size_t)ld * (by * B + c);
-#pragma unroll
-              for (int e = 0; e < E; ++e) {
-                X[c][e] = active ? cx[gl + G * e] : T(0);
-                Y[c][e] = active ? cy[gl + G * e] : T(0);
-              }
+              X[c].load(W + (size_t)ld * (bx * B + c), gl, active);
+              Y[c].load(W + (size_t)ld * (by * B + c), gl, active);
               nx[c] = active ? nrm2[bx * B + c] : T(0);
               ny[c] = active ? nrm2[by * B + c] : T(0);
             }
@@ -488,11 +581,11 @@ jacobi_svt_kernel(const JArgs a) {
 #pragma unroll
                 for (int kk = 0; kk < B / 2; ++kk) {
                   const int i = rr_i(r, kk, B), j = rr_j(r, kk, B);
-                  T g1 = group_dot<G>(X[i], X[j]), g2 = group_dot<G>(Y[i], Y[j]);
+                  T g1 = reg_dot(X[i], X[j]), g2 = reg_dot(Y[i], Y[j]);
                   g1 = group_sum<G>(g1);
                   g2 = group_sum<G>(g2);
-                  if (rotate_regs(X[i], X[j], nx[i], nx[j], g1, tol2)) { flag = 1; nrot += (gl == 0); }
-                  if (rotate_regs(Y[i], Y[j], ny[i], ny[j], g2, tol2)) { flag = 1; nrot += (gl == 0); }
+                  if (reg_rotate(X[i], X[j], nx[i], nx[j], g1, tol2)) { flag = 1; nrot += (gl == 0); }
+                  if (reg_rotate(Y[i], Y[j], ny[i], ny[j], g2, tol2)) { flag = 1; nrot += (gl == 0); }
                 }
               }
             }
@@ -500,12 +593,12 @@ jacobi_svt_kernel(const JArgs a) {
             for (int q = 0; q < B; ++q) {  // cross pairs (X_i, Y_{(i+q) mod B})
               T g[B];
 #pragma unroll
-              for (int i = 0; i < B; ++i) g[i] = group_dot<G>(X[i], Y[(i + q) % B]);
+              for (int i = 0; i < B; ++i) g[i] = reg_dot(X[i], Y[(i + q) % B]);
 #pragma unroll
               for (int i = 0; i < B; ++i) g[i] = group_sum<G>(g[i]);
 #pragma unroll
               for (int i = 0; i < B; ++i)
-                if (rotate_regs(X[i], Y[(i + q) % B], nx[i], ny[(i + q) % B], g[i], tol2)) {
+                if (reg_rotate(X[i], Y[(i + q) % B], nx[i], ny[(i + q) % B], g[i], tol2)) {
                   flag = 1;
                   nrot += (gl == 0);
                 }
@@ -513,13 +606,8 @@ jacobi_svt_kernel(const JArgs a) {
             if (active) {
 #pragma unroll
               for (int c = 0; c < B; ++c) {
-                T* cx = W + (size_t)ld * (bx * B + c);
-                T* cy = W + (size_t)ld * (by * B + c);
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                  cx[gl + G * e] = X[c][e];
-                  cy[gl + G * e] = Y[c][e];
-                }
+                X[c].store(W + (size_t)ld * (bx * B + c), gl);
+                Y[c].store(W + (size_t)ld * (by * B + c), gl);
                 if (gl == 0) {
                   nrm2[bx * B + c] = nx[c];
                   nrm2[by * B + c] = ny[c];
