@@ -59,14 +59,62 @@ struct PassArgs {
   int fuse_mode;      // FUSE_* for this pass
 };
 
-// FP32 mode products of one tile: a work item is (fiber, 8 consecutive outputs
-// j0..j0+7, 4 consecutive columns); per input index i one 16-byte load of x (4 columns)
-// and two of the coefficients feed 32 FMAs.  Items are ordered output chunk first, so
-// the 8 x 4 threads of a warp mostly share j0 (uniform coefficient loads).  Returns the
-// buffer holding the result.
-// One mode (index q of the pass) of the FP32 mode products of a tile, src -> dst; a work
-// item computes R consecutive outputs of a fibre for C = 4 columns (R = 8; R = 2 spreads
-// passes over few short fibres, e.g. a tile of 8 rows, over all warps).
+// FP32 mode products of one tile: a work item is (fiber, R consecutive outputs
+// j0..j0+R-1, C = 4 consecutive columns); per input index i one 16-byte load of x (4
+// columns) and the R coefficients feed 4 R FMAs (R = 8; R = 2 spreads passes over few
+// short fibres, e.g. a tile of 8 rows, over all warps).  Items are ordered output chunk
+// first, so the threads of a warp mostly share j0 (uniform coefficient loads).
+//
+// One work item: mode size I with stride st (in rows of the tile), coefficients MT
+// stored transposed with Ip padded rows, fibre start fbase, column group cg.
+template <int TS, int R>
+__device__ __forceinline__ void item_f32(int I, int st, int Ip, const float* MT, int fbase,
+                                         int j0, int cg, const float* src, float* dst) {
+  constexpr int C = 4;
+  float acc[R][C];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[r][c] = 0.f;
+  const float* xp = src + (size_t)fbase * TS + cg * C;
+  const float* mp = MT + j0;
+  for (int i = 0; i < I; ++i) {
+    const float4 x = *reinterpret_cast<const float4*>(xp + (size_t)st * i * TS);
+    float mv[R];
+    if constexpr (R == 8) {
+      const float4 m0 = *reinterpret_cast<const float4*>(mp + i * Ip);
+      const float4 m1 = *reinterpret_cast<const float4*>(mp + i * Ip + 4);
+      mv[0] = m0.x; mv[1] = m0.y; mv[2] = m0.z; mv[3] = m0.w;
+      mv[4] = m1.x; mv[5] = m1.y; mv[6] = m1.z; mv[7] = m1.w;
+    } else {
+      static_assert(R == 2, "R is 8 or 2");
+      const float2 m0 = *reinterpret_cast<const float2*>(mp + i * Ip);
+      mv[0] = m0.x; mv[1] = m0.y;
+    }
+    const float xv[C] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+      for (int c = 0; c < C; ++c) acc[r][c] = fmaf(mv[r], xv[c], acc[r][c]);
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (j0 + r < I)
+      *reinterpret_cast<float4*>(dst + (size_t)(fbase + st * (j0 + r)) * TS + cg * C) =
+          make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+}
+
+// Geometry of work item it of a mode (size I, stride st) of a pass with Pg rows.
+template <int R>
+__device__ __forceinline__ void item_geometry(int it, int I, int st, int Pg, int& fbase,
+                                              int& j0) {
+  const int nfib = Pg / I;
+  const int ch = it / nfib, fiber = it % nfib;
+  fbase = fiber % st + st * I * (fiber / st);
+  j0 = ch * R;
+}
+
+// One mode (index q of the pass) of the FP32 mode products of a tile, src -> dst.
 template <int TS, int R = 8>
 __device__ __forceinline__ void mode_f32(const TransformPass& p, int q, const float* mats_s,
                                          const int* moff_s, const float* src, float* dst) {
@@ -75,48 +123,13 @@ __device__ __forceinline__ void mode_f32(const TransformPass& p, int q, const fl
   const int cg = threadIdx.x % (TS / C);
   const int rs = threadIdx.x / (TS / C);
   const int nrs = blockDim.x / (TS / C);
-  {
-    const int I = p.msize[q], st = p.mstride[q], Ip = padded_rows(I);
-    const float* MT = mats_s + moff_s[q];
-    const int nch = (I + R - 1) / R, nfib = Pg / I;
-    const int items = nch * nfib;
-    for (int it = rs; it < items; it += nrs) {
-      const int ch = it / nfib, fiber = it % nfib;
-      const int aa = fiber % st, bb = fiber / st;
-      const int fbase = aa + st * I * bb;
-      const int j0 = ch * R;
-      float acc[R][C];
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int c = 0; c < C; ++c) acc[r][c] = 0.f;
-      const float* xp = src + (size_t)fbase * TS + cg * C;
-      const float* mp = MT + j0;
-      for (int i = 0; i < I; ++i) {
-        const float4 x = *reinterpret_cast<const float4*>(xp + (size_t)st * i * TS);
-        float mv[R];
-        if constexpr (R == 8) {
-          const float4 m0 = *reinterpret_cast<const float4*>(mp + i * Ip);
-          const float4 m1 = *reinterpret_cast<const float4*>(mp + i * Ip + 4);
-          mv[0] = m0.x; mv[1] = m0.y; mv[2] = m0.z; mv[3] = m0.w;
-          mv[4] = m1.x; mv[5] = m1.y; mv[6] = m1.z; mv[7] = m1.w;
-        } else {
-          static_assert(R == 2, "R is 8 or 2");
-          const float2 m0 = *reinterpret_cast<const float2*>(mp + i * Ip);
-          mv[0] = m0.x; mv[1] = m0.y;
-        }
-        const float xv[C] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-          for (int c = 0; c < C; ++c) acc[r][c] = fmaf(mv[r], xv[c], acc[r][c]);
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r)
-        if (j0 + r < I)
-          *reinterpret_cast<float4*>(dst + (size_t)(fbase + st * (j0 + r)) * TS + cg * C) =
-              make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-    }
+  const int I = p.msize[q], st = p.mstride[q], Ip = padded_rows(I);
+  const float* MT = mats_s + moff_s[q];
+  const int items = ((I + R - 1) / R) * (Pg / I);
+  for (int it = rs; it < items; it += nrs) {
+    int fbase, j0;
+    item_geometry<R>(it, I, st, Pg, fbase, j0);
+    item_f32<TS, R>(I, st, Ip, MT, fbase, j0, cg, src, dst);
   }
 }
 
@@ -488,7 +501,6 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
     mat_elems += p.msize[q] * padded_rows(p.msize[q]);
   }
   uint64_t* bars = reinterpret_cast<uint64_t*>(mats_s + ((mat_elems + 1) & ~1));
-  __shared__ int s_ok;
 
   // stage the matrices transposed with rows padded to a multiple of 8 (as transform_kernel)
   for (int q = 0; q < p.nm; ++q) {
@@ -513,23 +525,54 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
   const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
   const int64_t first = (int64_t)blockIdx.x * per;
   const int64_t mine = first < ntiles ? std::min<int64_t>(per, ntiles - first) : 0;
-  auto coords = [&](int64_t i, int& x, int& y) {
-    const int64_t t = first + i;
-    x = (int)((t % tpo) * TS);
-    y = (int)((t / tpo) * Pg);
+  // tile positions advance along a row of tiles, then to the next row group; the load and
+  // store cursors (thread 0) and the stage and phase of the waits are kept incrementally,
+  // with no 64-bit divisions per tile
+  struct Cursor {
+    int64_t xt, yt;
   };
+  const Cursor c0{first % tpo, first / tpo};
+  auto advance = [&](Cursor& c) {
+    if (++c.xt == tpo) { c.xt = 0; ++c.yt; }
+  };
+  // each thread's work item of the first two modes: the same for every tile when no row
+  // slot has more than one (true of the passes this form takes), so computed once
+  constexpr int C = 4;
+  const int cg = threadIdx.x % (TS / C), rs = threadIdx.x / (TS / C);
+  const int nrs = blockDim.x / (TS / C);
+  bool hoist = p.nm <= 2;
+  int hI[2], hst[2], hIp[2], hoff[2], hfb[2], hj0[2];
+  bool hon[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    hI[q] = hst[q] = hIp[q] = hfb[q] = hj0[q] = 0;
+    hoff[q] = q == 0 ? 0 : hI[0] * hIp[0];
+    hon[q] = false;
+    if (q < p.nm) {
+      hI[q] = p.msize[q];
+      hst[q] = p.mstride[q];
+      hIp[q] = padded_rows(hI[q]);
+      const int items = ((hI[q] + R - 1) / R) * (Pg / hI[q]);
+      if (items > nrs) hoist = false;
+      if (rs < items) {
+        item_geometry<R>(rs, hI[q], hst[q], Pg, hfb[q], hj0[q]);
+        hon[q] = true;
+      }
+    }
+  }
   int64_t issued = 0;  // tiles whose load thread 0 has issued
+  Cursor lc = c0, sc = c0;
   if (threadIdx.x == 0)
     for (; issued < stages && issued < mine; ++issued) {
-      int x, y;
-      coords(issued, x, y);
-      tma_load_tile(smem_addr(stage_buf) + (uint32_t)(issued % stages) * tile_pad, &map_in,
-                    smem_addr(bars + issued % stages), x, y, tile_bytes);
+      tma_load_tile(smem_addr(stage_buf) + (uint32_t)issued * tile_pad, &map_in,
+                    smem_addr(bars + issued), (int)(lc.xt * TS), (int)(lc.yt * Pg), tile_bytes);
+      advance(lc);
     }
   int64_t i = 0;
+  int s = 0;
+  uint32_t ph = 0;
   for (; i < mine; ++i) {
-    const int s = (int)(i % stages);
-    const bool ok = tma_mbar_wait(smem_addr(bars + s), (uint32_t)((i / stages) & 1));
+    const bool ok = tma_mbar_wait(smem_addr(bars + s), ph);
     if (!__syncthreads_and(ok)) {
       if (threadIdx.x == 0) atomicOr(status, LT_DEV_TIMEOUT);
       break;
@@ -542,29 +585,41 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
     // modes in turn, stage -> T -> stage -> ...; the result is in T after an odd number
     float* src = X;
     float* dst = tbuf;
-    for (int q = 0; q < p.nm; ++q) {
-      mode_f32<TS, R>(p, q, mats_s, moff_s, src, dst);
-      __syncthreads();
-      float* t = src; src = dst; dst = t;
+    if (hoist) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+        if (q < p.nm) {
+          if (hon[q])
+            item_f32<TS, R>(hI[q], hst[q], hIp[q], mats_s + hoff[q], hfb[q], hj0[q], cg, src, dst);
+          __syncthreads();
+          float* t = src; src = dst; dst = t;
+        }
+    } else {
+      for (int q = 0; q < p.nm; ++q) {
+        mode_f32<TS, R>(p, q, mats_s, moff_s, src, dst);
+        __syncthreads();
+        float* t = src; src = dst; dst = t;
+      }
     }
     // generic-proxy writes of the result (and reads of the stage) before the async-proxy
     // store and the next load into the stage
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
     if (threadIdx.x == 0) {
-      int x, y;
-      coords(i, x, y);
-      tma_store_tile(&map_out, smem_addr(src), x, y);
+      tma_store_tile(&map_out, smem_addr(src), (int)(sc.xt * TS), (int)(sc.yt * Pg));
+      advance(sc);
       // with the result in the stage, the stage takes its next load only after the store
-      // has read it (with the result in T the stage is free already)
+      // has read it (with the result in T the stage is free already); the load issued
+      // here is tile i + stages, whose stage is s
       if (!(p.nm & 1)) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       if (issued < mine) {
-        coords(issued, x, y);
         tma_load_tile(smem_addr(stage_buf) + (uint32_t)s * tile_pad, &map_in,
-                      smem_addr(bars + s), x, y, tile_bytes);
+                      smem_addr(bars + s), (int)(lc.xt * TS), (int)(lc.yt * Pg), tile_bytes);
+        advance(lc);
         ++issued;
       }
     }
+    if (++s == stages) { s = 0; ph ^= 1u; }
   }
   if (threadIdx.x == 0) {
     // after an expired wait, the loads still in flight (that tile's included) land before
