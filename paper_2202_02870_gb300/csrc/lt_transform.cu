@@ -122,7 +122,7 @@ __device__ __forceinline__ void mode_f32(const TransformPass& p, int q, const fl
   const int Pg = (int)p.Pg;
   const int cg = threadIdx.x % (TS / C);
   const int rs = threadIdx.x / (TS / C);
-  const int nrs = blockDim.x / (TS / C);
+  const int nrs = kThreads / (TS / C);  // the compute threads of either kernel
   const int I = p.msize[q], st = p.mstride[q], Ip = padded_rows(I);
   const float* MT = mats_s + moff_s[q];
   const int items = ((I + R - 1) / R) * (Pg / I);
@@ -421,17 +421,39 @@ size_t smem_bytes(const TransformPass& p, int ts) {
 // ---------------------------------------------------------------------------------
 // Plain FP32 passes through the tensor memory accelerator.  The view [outer][Pg][Sg]
 // is a 2-D tensor of Pg * outer rows of Sg floats, and a tile (Pg rows x TS columns of
-// one outer block) is one TMA box: thread 0 keeps up to kTmaStages tiles in flight into a
-// ring of shared-memory stages (mbarrier complete_tx), every thread computes the mode
-// products of the current tile between its stage and one scratch buffer, and thread 0
-// writes the result back with one TMA store; once the store has read it, the stage takes
-// the load of a later tile.  Two CTAs share an SM (two tiles' mode products in flight).
-// The arithmetic is mode_f32's, so the results equal the SIMT pass bit for bit.  Every
-// wait on an mbarrier is bounded (1 s; then LT_DEV_TIMEOUT, the loop stops, the loads in
-// flight are drained with bounded waits and the stores completed before the CTA exits).
+// one outer block) is one TMA box.  A CTA is eight compute warps and one copy warp: one
+// thread of the copy warp keeps up to kTmaStages tiles in flight into a ring of
+// shared-memory stages (mbarrier complete_tx), writes each finished tile back with one
+// TMA store and, once the store has read it, gives the buffer back (the stage to the load
+// of a later tile; with an odd number of modes the result sits in one of two scratch
+// tiles, which a "free" mbarrier returns to the compute warps).  The compute warps wait
+// for a stage, run the mode products between the stage and scratch, synchronise among
+// themselves on a named barrier and signal "done"; they never wait for a store.  Two CTAs
+// share an SM.  The arithmetic is mode_f32's, so the results equal the SIMT pass bit for
+// bit.  Every wait on an mbarrier is bounded (1 s; then LT_DEV_TIMEOUT, both roles stop,
+// the loads in flight are drained with bounded waits and the stores completed before the
+// copy thread exits).
 // ---------------------------------------------------------------------------------
 constexpr int kTmaStages = 8;
 constexpr unsigned long long kTmaWaitNs = 1000000000ull;
+constexpr int kTmaThreads = kThreads + 32;  // eight compute warps and one copy warp
+
+// named barrier 1 over the compute warps; the AND form agrees on a flag
+__device__ __forceinline__ void compute_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory");
+}
+__device__ __forceinline__ bool compute_all(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.and.pred q, 1, %2, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"((uint32_t)v), "n"(kThreads)
+      : "memory");
+  return r != 0;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -470,6 +492,9 @@ __device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* m
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 __device__ __forceinline__ void tma_store_tile(const CUtensorMap* map, uint32_t src, int x, int y) {
   asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                    reinterpret_cast<uint64_t>(map)),
@@ -479,7 +504,7 @@ __device__ __forceinline__ void tma_store_tile(const CUtensorMap* map, uint32_t 
 }
 
 template <int TS, int R>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kTmaThreads, 2)
 transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
                      const __grid_constant__ CUtensorMap map_out, const PassArgs a,
                      int stages, int32_t* status) {
@@ -488,19 +513,23 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
   const int Pg = (int)p.Pg;
   const uint32_t tile_bytes = (uint32_t)Pg * TS * 4;
   const uint32_t tile_pad = (tile_bytes + 1023u) & ~1023u;
-  // [stages][T] tiles (1024-byte aligned), the matrices, the barriers
+  // [stages][T] tiles (1024-byte aligned; two T tiles when the number of modes is odd),
+  // the matrices, the barriers: full[stages], done[stages], tfree[2]
+  const int nt = (p.nm & 1) ? 2 : 1;
   const uint32_t raw = smem_addr(tma_smem);
   unsigned char* base = tma_smem + (((raw + 1023u) & ~1023u) - raw);
   float* stage_buf = reinterpret_cast<float*>(base);
-  float* tbuf = reinterpret_cast<float*>(base + (size_t)stages * tile_pad);
-  float* mats_s = reinterpret_cast<float*>(base + (size_t)(stages + 1) * tile_pad);
+  float* tbuf0 = reinterpret_cast<float*>(base + (size_t)stages * tile_pad);
+  float* mats_s = reinterpret_cast<float*>(base + (size_t)(stages + nt) * tile_pad);
   int moff_s[kMaxModes];
   int mat_elems = 0;
   for (int q = 0; q < p.nm; ++q) {
     moff_s[q] = mat_elems;
     mat_elems += p.msize[q] * padded_rows(p.msize[q]);
   }
-  uint64_t* bars = reinterpret_cast<uint64_t*>(mats_s + ((mat_elems + 1) & ~1));
+  uint64_t* full = reinterpret_cast<uint64_t*>(mats_s + ((mat_elems + 1) & ~1));
+  uint64_t* done = full + stages;
+  uint64_t* tfree = done + stages;
 
   // stage the matrices transposed with rows padded to a multiple of 8 (as transform_kernel)
   for (int q = 0; q < p.nm; ++q) {
@@ -512,11 +541,11 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
     }
   }
   if (threadIdx.x == 0) {
-    for (int s = 0; s < stages; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bars + s)) : "memory");
+    for (int b = 0; b < 2 * stages + 2; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(full + b)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();
+  __syncthreads();  // the last barrier of all threads: the roles part here
 
   // a CTA takes a contiguous run of tiles (consecutive column ranges of the same rows),
   // so that every row of its tiles is read and written in long runs
@@ -525,110 +554,110 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
   const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
   const int64_t first = (int64_t)blockIdx.x * per;
   const int64_t mine = first < ntiles ? std::min<int64_t>(per, ntiles - first) : 0;
-  // tile positions advance along a row of tiles, then to the next row group; the load and
-  // store cursors (thread 0) and the stage and phase of the waits are kept incrementally,
-  // with no 64-bit divisions per tile
-  struct Cursor {
-    int64_t xt, yt;
-  };
-  const Cursor c0{first % tpo, first / tpo};
-  auto advance = [&](Cursor& c) {
-    if (++c.xt == tpo) { c.xt = 0; ++c.yt; }
-  };
-  // each thread's work item of the first two modes: the same for every tile when no row
-  // slot has more than one (true of the passes this form takes), so computed once
-  constexpr int C = 4;
-  const int cg = threadIdx.x % (TS / C), rs = threadIdx.x / (TS / C);
-  const int nrs = blockDim.x / (TS / C);
-  bool hoist = p.nm <= 2;
-  int hI[2], hst[2], hIp[2], hoff[2], hfb[2], hj0[2];
-  bool hon[2];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    hI[q] = hst[q] = hIp[q] = hfb[q] = hj0[q] = 0;
-    hoff[q] = q == 0 ? 0 : hI[0] * hIp[0];
-    hon[q] = false;
-    if (q < p.nm) {
-      hI[q] = p.msize[q];
-      hst[q] = p.mstride[q];
-      hIp[q] = padded_rows(hI[q]);
-      const int items = ((hI[q] + R - 1) / R) * (Pg / hI[q]);
-      if (items > nrs) hoist = false;
-      if (rs < items) {
-        item_geometry<R>(rs, hI[q], hst[q], Pg, hfb[q], hj0[q]);
-        hon[q] = true;
-      }
-    }
-  }
-  int64_t issued = 0;  // tiles whose load thread 0 has issued
-  Cursor lc = c0, sc = c0;
-  if (threadIdx.x == 0)
+
+  if (threadIdx.x >= kThreads) {
+    // ---- copy warp: one thread issues every load and store
+    if (threadIdx.x != kThreads) return;
+    // tile positions advance along a row of tiles, then to the next row group (kept
+    // incrementally, no 64-bit divisions per tile)
+    int64_t lxt = first % tpo, lyt = first / tpo, sxt = lxt, syt = lyt;
+    int64_t issued = 0;
     for (; issued < stages && issued < mine; ++issued) {
       tma_load_tile(smem_addr(stage_buf) + (uint32_t)issued * tile_pad, &map_in,
-                    smem_addr(bars + issued), (int)(lc.xt * TS), (int)(lc.yt * Pg), tile_bytes);
-      advance(lc);
+                    smem_addr(full + issued), (int)(lxt * TS), (int)(lyt * Pg), tile_bytes);
+      if (++lxt == tpo) { lxt = 0; ++lyt; }
     }
-  int64_t i = 0;
+    int64_t i = 0;
+    int s = 0;
+    uint32_t ph = 0;
+    for (; i < mine; ++i) {
+      if (!tma_mbar_wait(smem_addr(done + s), ph)) {
+        atomicOr(status, LT_DEV_TIMEOUT);
+        break;
+      }
+      const uint32_t res = (p.nm & 1) ? smem_addr(tbuf0) + (uint32_t)(i & 1) * tile_pad
+                                      : smem_addr(stage_buf) + (uint32_t)s * tile_pad;
+      tma_store_tile(&map_out, res, (int)(sxt * TS), (int)(syt * Pg));
+      if (++sxt == tpo) { sxt = 0; ++syt; }
+      // the stage takes tile i + stages: at once when the result is in T (the mode
+      // products only read the stage), else once the store has read it
+      if (!(p.nm & 1)) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      if (issued < mine) {
+        tma_load_tile(smem_addr(stage_buf) + (uint32_t)s * tile_pad, &map_in, smem_addr(full + s),
+                      (int)(lxt * TS), (int)(lyt * Pg), tile_bytes);
+        if (++lxt == tpo) { lxt = 0; ++lyt; }
+        ++issued;
+      }
+      if (p.nm & 1) {  // T(i & 1) goes back to the compute warps for tile i + 2
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        mbar_arrive(smem_addr(tfree + (i & 1)));
+      }
+      if (++s == stages) { s = 0; ph ^= 1u; }
+    }
+    // after an expired wait, the loads still in flight land before the thread exits
+    for (int64_t j = i; j < issued; ++j)
+      tma_mbar_wait(smem_addr(full + j % stages), (uint32_t)((j / stages) & 1));
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    return;
+  }
+
+  // ---- compute warps.  Each thread's work item of the first two modes is the same for
+  // every tile when no row slot has more than one (true of the passes this form takes),
+  // so it is computed once.
+  constexpr int C = 4;
+  const int cg = threadIdx.x % (TS / C), rs = threadIdx.x / (TS / C);
+  const int nrs = kThreads / (TS / C);
+  // (the mode sizes and strides are kernel parameters, re-read per tile; only the item's
+  // fibre start and first output stay in registers, -1 when the thread has none)
+  bool hoist = p.nm <= 2;
+  int hfb[2] = {-1, -1}, hj0[2] = {0, 0};
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+    if (q < p.nm) {
+      const int I = p.msize[q];
+      const int items = ((I + R - 1) / R) * (Pg / I);
+      if (items > nrs) hoist = false;
+      if (rs < items) item_geometry<R>(rs, I, p.mstride[q], Pg, hfb[q], hj0[q]);
+    }
   int s = 0;
   uint32_t ph = 0;
-  for (; i < mine; ++i) {
-    const bool ok = tma_mbar_wait(smem_addr(bars + s), ph);
-    if (!__syncthreads_and(ok)) {
+  for (int64_t i = 0; i < mine; ++i) {
+    bool ok = tma_mbar_wait(smem_addr(full + s), ph);
+    // the scratch tile this one's result goes to was stored two tiles ago
+    if ((p.nm & 1) && i >= 2)
+      ok = ok && tma_mbar_wait(smem_addr(tfree + (i & 1)), (uint32_t)(((i >> 1) - 1) & 1));
+    if (!compute_all(ok)) {
       if (threadIdx.x == 0) atomicOr(status, LT_DEV_TIMEOUT);
       break;
     }
-    // an odd number of modes leaves the result in T: the store of the previous tile must
-    // have read it before T is written again
-    if ((p.nm & 1) && threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-    __syncthreads();
-    float* X = stage_buf + (size_t)s * (tile_pad / 4);
     // modes in turn, stage -> T -> stage -> ...; the result is in T after an odd number
-    float* src = X;
-    float* dst = tbuf;
+    float* src = stage_buf + (size_t)s * (tile_pad / 4);
+    float* dst = tbuf0 + (size_t)(i & (nt - 1)) * (tile_pad / 4);
     if (hoist) {
 #pragma unroll
       for (int q = 0; q < 2; ++q)
         if (q < p.nm) {
-          if (hon[q])
-            item_f32<TS, R>(hI[q], hst[q], hIp[q], mats_s + hoff[q], hfb[q], hj0[q], cg, src, dst);
-          __syncthreads();
+          const int I = p.msize[q];
+          const float* MT = mats_s + (q == 0 ? 0 : p.msize[0] * padded_rows(p.msize[0]));
+          if (hfb[q] >= 0)
+            item_f32<TS, R>(I, p.mstride[q], padded_rows(I), MT, hfb[q], hj0[q], cg, src, dst);
+          compute_sync();
           float* t = src; src = dst; dst = t;
         }
     } else {
       for (int q = 0; q < p.nm; ++q) {
         mode_f32<TS, R>(p, q, mats_s, moff_s, src, dst);
-        __syncthreads();
+        compute_sync();
         float* t = src; src = dst; dst = t;
       }
     }
-    // generic-proxy writes of the result (and reads of the stage) before the async-proxy
-    // store and the next load into the stage
+    // generic-proxy writes of the result and reads of the stage before the copy thread's
+    // async-proxy store and its next load into the stage
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      tma_store_tile(&map_out, smem_addr(src), (int)(sc.xt * TS), (int)(sc.yt * Pg));
-      advance(sc);
-      // with the result in the stage, the stage takes its next load only after the store
-      // has read it (with the result in T the stage is free already); the load issued
-      // here is tile i + stages, whose stage is s
-      if (!(p.nm & 1)) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-      if (issued < mine) {
-        tma_load_tile(smem_addr(stage_buf) + (uint32_t)s * tile_pad, &map_in,
-                      smem_addr(bars + s), (int)(lc.xt * TS), (int)(lc.yt * Pg), tile_bytes);
-        advance(lc);
-        ++issued;
-      }
-    }
+    compute_sync();
+    if (threadIdx.x == 0) mbar_arrive(smem_addr(done + s));
     if (++s == stages) { s = 0; ph ^= 1u; }
   }
-  if (threadIdx.x == 0) {
-    // after an expired wait, the loads still in flight (that tile's included) land before
-    // the CTA exits
-    for (int64_t j = i; j < issued; ++j)
-      tma_mbar_wait(smem_addr(bars + j % stages), (uint32_t)((j / stages) & 1));
-    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-  }
-  __syncthreads();
 }
 
 template <typename T, int TS>
@@ -713,17 +742,17 @@ cudaError_t launch_tma_t(const Ctx& c, const PassArgs& a, const CUtensorMap& mi,
   for (int q = 0; q < p.nm; ++q) mats += (size_t)p.msize[q] * padded_rows(p.msize[q]) * 4;
   mats = (mats + 15) & ~size_t(15);
   // two CTAs per SM: half of the SM's shared memory each, less the per-CTA reservation
-  const size_t fixed = 1024 + tile_pad + mats;
+  const size_t fixed = 1024 + ((p.nm & 1) ? 2 : 1) * tile_pad + mats;
   const size_t limit = (size_t)kSmemOptin / 2 - 2048;
-  if (fixed + 2 * tile_pad + 8 * 2 > limit) return cudaErrorNotSupported;
-  int stages = (int)std::min<size_t>(kTmaStages, (limit - fixed) / (tile_pad + 8));
-  const size_t smem = fixed + (size_t)stages * tile_pad + 8 * (size_t)stages + 8;
+  if (fixed + 2 * tile_pad + 16 * 2 + 24 > limit) return cudaErrorNotSupported;
+  int stages = (int)std::min<size_t>(kTmaStages, (limit - fixed - 24) / (tile_pad + 16));
+  const size_t smem = fixed + (size_t)stages * tile_pad + 8 * (2 * (size_t)stages + 2) + 8;
   auto k = transform_tma_kernel<TS, R>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t tiles = p.outer * ((p.Sg + TS - 1) / TS);
   const int64_t grid = std::min<int64_t>(tiles, 2 * (int64_t)c.sms);
-  k<<<(unsigned)grid, kThreads, smem, st>>>(mi, mo, a, stages, c.d_status);
+  k<<<(unsigned)grid, kTmaThreads, smem, st>>>(mi, mo, a, stages, c.d_status);
   return cudaGetLastError();
 }
 
