@@ -15,10 +15,12 @@
 // general element strides, so that every transpose is free):
 //   C^p(m, n) = sum_k A^p(m, kk) B^p(k, n),  kk = kperm ? kperm[p K + k] : k,
 // with A^p(m, k) = A[p sap + m sam + k sak], B^p(k, n) = B[p sbp + k sbk + n sbn],
-// C^p(m, n) = C[p scp + m scm + n scn]; 64 x 64 output tile per CTA, 16-deep K steps in
-// shared memory, 4 x 4 register tile per thread; and the scatter that turns the first
-// basis (Q = I) into P W.  Every kernel returns at once when the PGA run has already
-// met its tolerance.
+// C^p(m, n) = C[p scp + m scm + n scn]; one output tile per CTA (FP64 48 x 48 with a
+// 3 x 3 register tile per thread: the FP64 pipe bounds the product, and 48 divides the
+// slice sizes of the benchmark, 144, where 64 x 64 tiles computed up to 44 % padding;
+// FP32 64 x 64 with 4 x 4), 16-deep K steps in shared memory; and the scatter that turns
+// the first basis (Q = I) into P W.  Every kernel returns at once when the PGA run has
+// already met its tolerance.
 #include <algorithm>
 
 #include "lt_internal.cuh"
@@ -26,13 +28,15 @@
 namespace lt {
 namespace {
 
-constexpr int WBM = 64, WBN = 64, WBK = 16, WTM = 4, WTN = 4;
-constexpr int kWThreads = (WBM / WTM) * (WBN / WTN);  // 256
+constexpr int WBK = 16;
+constexpr int kWThreads = 256;
 
-template <typename T>
+template <typename T, int WBM, int WTM>
 __global__ void __launch_bounds__(kWThreads)
 strided_gemm_kernel(const StridedGemm g, const T* __restrict__ A, const T* __restrict__ B,
                     T* __restrict__ C, const PgaScalars* scal) {
+  constexpr int WBN = WBM, WTN = WTM;
+  static_assert((WBM / WTM) * (WBN / WTN) == kWThreads, "one register tile per thread");
   if (scal != nullptr && scal->done) return;
   __shared__ T As[WBK][WBM];
   __shared__ T Bs[WBK][WBN + 1];
@@ -110,13 +114,14 @@ cudaError_t launch_strided_gemm(const Ctx& c, const StridedGemm& g, const void* 
                                 cudaStream_t st) {
   if (g.M < 1 || g.N < 1 || g.K < 1 || g.P < 1) return cudaErrorInvalidValue;
   const int64_t gz = g.P < 65535 ? g.P : 65535;
-  dim3 grid((unsigned)((g.M + WBM - 1) / WBM), (unsigned)((g.N + WBN - 1) / WBN), (unsigned)gz);
+  const int64_t tile = c.elem == 8 ? 48 : 64;
+  dim3 grid((unsigned)((g.M + tile - 1) / tile), (unsigned)((g.N + tile - 1) / tile), (unsigned)gz);
   if (c.elem == 8)
-    strided_gemm_kernel<double><<<grid, kWThreads, 0, st>>>(
+    strided_gemm_kernel<double, 48, 3><<<grid, kWThreads, 0, st>>>(
         g, static_cast<const double*>(A), static_cast<const double*>(B),
         static_cast<double*>(C), scal);
   else
-    strided_gemm_kernel<float><<<grid, kWThreads, 0, st>>>(
+    strided_gemm_kernel<float, 64, 4><<<grid, kWThreads, 0, st>>>(
         g, static_cast<const float*>(A), static_cast<const float*>(B), static_cast<float*>(C),
         scal);
   return cudaGetLastError();
