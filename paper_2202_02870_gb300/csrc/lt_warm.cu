@@ -15,12 +15,11 @@
 // general element strides, so that every transpose is free):
 //   C^p(m, n) = sum_k A^p(m, kk) B^p(k, n),  kk = kperm ? kperm[p K + k] : k,
 // with A^p(m, k) = A[p sap + m sam + k sak], B^p(k, n) = B[p sbp + k sbk + n sbn],
-// C^p(m, n) = C[p scp + m scm + n scn]; one output tile per CTA (FP64 48 x 48 with a
-// 3 x 3 register tile per thread: the FP64 pipe bounds the product, and 48 divides the
-// slice sizes of the benchmark, 144, where 64 x 64 tiles computed up to 44 % padding;
-// FP32 64 x 64 with 4 x 4), 16-deep K steps in shared memory; and the scatter that turns
-// the first basis (Q = I) into P W.  Every kernel returns at once when the PGA run has
-// already met its tolerance.
+// C^p(m, n) = C[p scp + m scm + n scn]; one 48 x 48 output tile per CTA with a 3 x 3
+// register tile per thread (48 divides the slice sizes of the benchmark, 144, where
+// 64 x 64 tiles computed up to 44 % padding), 16-deep K steps in shared memory; and the
+// scatter that turns the first basis (Q = I) into P W.  Every kernel returns at once when
+// the PGA run has already met its tolerance.
 #include <algorithm>
 
 #include "lt_internal.cuh"
@@ -114,14 +113,14 @@ cudaError_t launch_strided_gemm(const Ctx& c, const StridedGemm& g, const void* 
                                 cudaStream_t st) {
   if (g.M < 1 || g.N < 1 || g.K < 1 || g.P < 1) return cudaErrorInvalidValue;
   const int64_t gz = g.P < 65535 ? g.P : 65535;
-  const int64_t tile = c.elem == 8 ? 48 : 64;
+  const int64_t tile = 48;
   dim3 grid((unsigned)((g.M + tile - 1) / tile), (unsigned)((g.N + tile - 1) / tile), (unsigned)gz);
   if (c.elem == 8)
     strided_gemm_kernel<double, 48, 3><<<grid, kWThreads, 0, st>>>(
         g, static_cast<const double*>(A), static_cast<const double*>(B),
         static_cast<double*>(C), scal);
   else
-    strided_gemm_kernel<float, 64, 4><<<grid, kWThreads, 0, st>>>(
+    strided_gemm_kernel<float, 48, 3><<<grid, kWThreads, 0, st>>>(
         g, static_cast<const float*>(A), static_cast<const float*>(B), static_cast<float*>(C),
         scal);
   return cudaGetLastError();
