@@ -145,8 +145,8 @@ def profiled_traffic(kernel):
     return None
 
 
-# HBM copy bandwidth of the GB300s as the driver measured it at the start of the
-# work (MEASURED_PEAKS.json, hbm_gbs); used when that file is not present on the box.
+# HBM copy bandwidth of a GB300 as recorded in MEASURED_PEAKS.json (hbm_gbs) before this
+# code was tuned; used when that file is not present.
 HBM_GBS_RECORDED = 6799.6
 
 
