@@ -163,7 +163,7 @@ def hbm_peak():
     v = load_peaks().get("hbm_gbs")
     if v:
         return float(v), "MEASURED_PEAKS.json hbm_gbs (of measured)"
-    return HBM_GBS_RECORDED, "this pool's measured copy bandwidth as recorded (of measured)"
+    return HBM_GBS_RECORDED, "MEASURED_PEAKS.json hbm_gbs as recorded in bench.py (of measured)"
 
 
 def dist_env():
