@@ -131,17 +131,19 @@ typedef enum {
                                 thread-block cluster of that many CTAs per slice (columns
                                 spread over the CTAs' shared memory; slices up to 288
                                 columns after padding) */
-  LT_OPT_TC_WAIT_US = 11,    /* LT_MIXED: limit of every bounded wait inside the
-                                tensor-core kernel, in microseconds (0 = default, 1 s;
-                                at most 60 s).  On expiry the kernel raises
+  LT_OPT_TC_WAIT_US = 11,    /* limit of every bounded wait inside the TMA-fed kernels
+                                (the LT_MIXED tensor-core kernel and the FP32 TMA
+                                transform passes), in microseconds (0 = default, 1 s;
+                                at most 60 s).  On expiry a kernel raises
                                 LT_DEV_TIMEOUT, stops issuing work, drains the copies and
                                 products it has in flight, frees its TMEM and returns;
                                 its output is then undefined. */
-  LT_OPT_TC_TEST_NO_LOADS = 12, /* LT_MIXED, for testing the timeout path only: 1 = the
-                                tensor-core kernel's producer issues no copies, so the
-                                other roles' first waits expire after LT_OPT_TC_WAIT_US
-                                and every call that reaches the kernel reports
-                                LT_DEV_TIMEOUT with undefined output; 0 (default) = off */
+  LT_OPT_TC_TEST_NO_LOADS = 12, /* for testing the timeout path only: 1 = the producers
+                                of the TMA-fed kernels (tensor-core kernel, TMA transform
+                                passes) issue no copies, so the other roles' first waits
+                                expire after LT_OPT_TC_WAIT_US and every call that
+                                reaches such a kernel reports LT_DEV_TIMEOUT with
+                                undefined output; 0 (default) = off */
   LT_OPT_TRANSFORM_TMA = 15, /* FP32 / LT_MIXED mode-product passes outside the PGA
                                 loop (lt_transform, lt_inverse, lt_product, lt_svt, ...):
                                 1 (default) = tiles move through the tensor memory

@@ -430,9 +430,9 @@ size_t smem_bytes(const TransformPass& p, int ts) {
 // for a stage, run the mode products between the stage and scratch, synchronise among
 // themselves on a named barrier and signal "done"; they never wait for a store.  Two CTAs
 // share an SM.  The arithmetic is mode_f32's, so the results equal the SIMT pass bit for
-// bit.  Every wait on an mbarrier is bounded (1 s; then LT_DEV_TIMEOUT, both roles stop,
-// the loads in flight are drained with bounded waits and the stores completed before the
-// copy thread exits).
+// bit.  Every wait on an mbarrier is bounded (1 s, or LT_OPT_TC_WAIT_US; then
+// LT_DEV_TIMEOUT, both roles stop, the loads in flight are drained with bounded waits and
+// the stores completed before the copy thread exits).
 // ---------------------------------------------------------------------------------
 constexpr int kTmaStages = 8;
 constexpr unsigned long long kTmaWaitNs = 1000000000ull;
@@ -470,7 +470,8 @@ __device__ __forceinline__ bool tma_mbar_try(uint32_t a, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for the phase of the given parity; false after kTmaWaitNs.
-__device__ bool tma_mbar_wait(uint32_t a, uint32_t parity) {
+__device__ bool tma_mbar_wait(uint32_t a, uint32_t parity,
+                              unsigned long long limit_ns = kTmaWaitNs) {
   if (tma_mbar_try(a, parity)) return true;
   unsigned long long t0, t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
@@ -478,7 +479,7 @@ __device__ bool tma_mbar_wait(uint32_t a, uint32_t parity) {
     if (tma_mbar_try(a, parity)) return true;
     if ((i & 127u) == 0) {
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-      if (t - t0 > kTmaWaitNs) return false;
+      if (t - t0 > limit_ns) return false;
     }
   }
 }
@@ -507,7 +508,7 @@ template <int TS, int R>
 __global__ void __launch_bounds__(kTmaThreads, 2)
 transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
                      const __grid_constant__ CUtensorMap map_out, const PassArgs a,
-                     int stages, int32_t* status) {
+                     int stages, int32_t* status, unsigned long long wait_ns, int no_loads) {
   extern __shared__ __align__(16) unsigned char tma_smem[];
   const TransformPass& p = a.p;
   const int Pg = (int)p.Pg;
@@ -562,7 +563,8 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
     // incrementally, no 64-bit divisions per tile)
     int64_t lxt = first % tpo, lyt = first / tpo, sxt = lxt, syt = lyt;
     int64_t issued = 0;
-    for (; issued < stages && issued < mine; ++issued) {
+    // (test switch: no loads at all, so that the compute warps' first waits expire)
+    for (; !no_loads && issued < stages && issued < mine; ++issued) {
       tma_load_tile(smem_addr(stage_buf) + (uint32_t)issued * tile_pad, &map_in,
                     smem_addr(full + issued), (int)(lxt * TS), (int)(lyt * Pg), tile_bytes);
       if (++lxt == tpo) { lxt = 0; ++lyt; }
@@ -571,7 +573,7 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
     int s = 0;
     uint32_t ph = 0;
     for (; i < mine; ++i) {
-      if (!tma_mbar_wait(smem_addr(done + s), ph)) {
+      if (!tma_mbar_wait(smem_addr(done + s), ph, wait_ns)) {
         atomicOr(status, LT_DEV_TIMEOUT);
         break;
       }
@@ -582,7 +584,7 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
       // the stage takes tile i + stages: at once when the result is in T (the mode
       // products only read the stage), else once the store has read it
       if (!(p.nm & 1)) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-      if (issued < mine) {
+      if (!no_loads && issued < mine) {
         tma_load_tile(smem_addr(stage_buf) + (uint32_t)s * tile_pad, &map_in, smem_addr(full + s),
                       (int)(lxt * TS), (int)(lyt * Pg), tile_bytes);
         if (++lxt == tpo) { lxt = 0; ++lyt; }
@@ -596,7 +598,7 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
     }
     // after an expired wait, the loads still in flight land before the thread exits
     for (int64_t j = i; j < issued; ++j)
-      tma_mbar_wait(smem_addr(full + j % stages), (uint32_t)((j / stages) & 1));
+      tma_mbar_wait(smem_addr(full + j % stages), (uint32_t)((j / stages) & 1), wait_ns);
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     return;
   }
@@ -622,10 +624,10 @@ transform_tma_kernel(const __grid_constant__ CUtensorMap map_in,
   int s = 0;
   uint32_t ph = 0;
   for (int64_t i = 0; i < mine; ++i) {
-    bool ok = tma_mbar_wait(smem_addr(full + s), ph);
+    bool ok = tma_mbar_wait(smem_addr(full + s), ph, wait_ns);
     // the scratch tile this one's result goes to was stored two tiles ago
     if ((p.nm & 1) && i >= 2)
-      ok = ok && tma_mbar_wait(smem_addr(tfree + (i & 1)), (uint32_t)(((i >> 1) - 1) & 1));
+      ok = ok && tma_mbar_wait(smem_addr(tfree + (i & 1)), (uint32_t)(((i >> 1) - 1) & 1), wait_ns);
     if (!compute_all(ok)) {
       if (threadIdx.x == 0) atomicOr(status, LT_DEV_TIMEOUT);
       break;
@@ -752,7 +754,10 @@ cudaError_t launch_tma_t(const Ctx& c, const PassArgs& a, const CUtensorMap& mi,
   if (e != cudaSuccess) return e;
   const int64_t tiles = p.outer * ((p.Sg + TS - 1) / TS);
   const int64_t grid = std::min<int64_t>(tiles, 2 * (int64_t)c.sms);
-  k<<<(unsigned)grid, kTmaThreads, smem, st>>>(mi, mo, a, stages, c.d_status);
+  const unsigned long long wait_ns =
+      c.tc_wait_us > 0 ? (unsigned long long)(c.tc_wait_us * 1e3) : kTmaWaitNs;
+  k<<<(unsigned)grid, kTmaThreads, smem, st>>>(mi, mo, a, stages, c.d_status, wait_ns,
+                                               c.tc_no_loads);
   return cudaGetLastError();
 }
 

@@ -235,6 +235,33 @@ def test_tc_bounded_wait_expires_then_context_recovers():
     assert rel(from_dev(Cd, (128, 64, 3)), O.product(A, B, oracle_mats(tr))) <= TOL
 
 
+def test_tma_transform_bounded_wait_expires_then_context_recovers():
+    """Failure detection of the TMA transform passes without a GPU fault: with the test
+    switch LT_OPT_TC_TEST_NO_LOADS the copy warp issues no loads, so the compute warps'
+    first waits (limit 5 ms) expire, they agree on it on their named barrier and stop, and
+    the copy thread's wait for their first tile expires in turn (nothing in flight).  The
+    call reports LT_DEV_TIMEOUT through the device status word; with the switch off the
+    same context then transforms correctly (both passes, {16, 16} and {8})."""
+    rng = np.random.default_rng(516)
+    full = (24, 20, 16, 16, 8)
+    X = rng.uniform(-1, 1, full)
+    tr = [("dct", 16), ("matrix", synth.conditioned_matrix(rng, 16, 10.0, True)), ("dct", 8)]
+    ctx = make_ctx(tr, lt.LT_FP32)
+    Xd = to_dev(X, torch.float32)
+    Y = empty_dev(full, torch.float32)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_WAIT_US, 5000)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_TEST_NO_LOADS, 1)
+    lt.lt_transform(ctx, Xd, Y)
+    torch.cuda.synchronize()
+    assert lt.lt_last_device_status(ctx) & lt.LT_DEV_TIMEOUT
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_TEST_NO_LOADS, 0)
+    lt.lt_ctx_set_option(ctx, lt.LT_OPT_TC_WAIT_US, 0)
+    lt.lt_transform(ctx, Xd, Y)
+    torch.cuda.synchronize()
+    assert lt.lt_last_device_status(ctx) == 0
+    assert rel(from_dev(Y, full), O.transform(X, oracle_mats(tr))) <= 1e-6
+
+
 # (I1, I2, trailing): a 256-slice pass of two modes plus a single-mode pass with wide tiles
 # (16, 16, 8), ragged tiles (Sg = 468), a single mode of 8, a view that is not a multiple
 # of 4 (SIMT fallback), and mode sizes 3 and 32 (one pass of 96 slices)
