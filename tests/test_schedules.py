@@ -4,7 +4,9 @@ half-blocks moved on a round-robin tournament) and the gather / scatter of the F
 operator's slots.  They guard the design: every column pair must meet once per sweep,
 the pairs of a local round must be disjoint, the chunked half-block moves must read each
 offset before its holder overwrites it, and the realified slices must carry
-[[a1, -a2], [a2, a1]] and scatter back to the slots exactly.
+[[a1, -a2], [a2, a1]] and scatter back to the slots exactly.  Also: the TMA transform
+kernel's incremental tile cursors and its per-thread work items, the FP32 sweeps' layout
+of rows in register pairs, and the ordering of the QR pivot keys.
 """
 import numpy as np
 import pytest
@@ -159,3 +161,126 @@ def test_fourier_realify_layout_and_round_trip(I1, I2, n, R):
             got = Wc[q * 4 * S:(q + 1) * 4 * S].reshape(2 * I2, 2 * I1).T
             assert np.array_equal(got, np.block([[a1, -a2], [a2, a1]]))
     assert np.array_equal(derealify(Wr, Wc, I1, I2, n, R), G)
+
+
+# ---- TMA transform passes: tile cursors and per-thread work items (lt_transform.cu)
+
+KTHREADS = 256  # compute threads of a transform CTA
+
+
+@pytest.mark.parametrize("Sg,TS,outer,grid", [(480, 32, 1, 304), (65536, 32, 1, 304),
+                                             (16777216 // 8, 256, 1, 304), (468, 32, 3, 7),
+                                             (4096, 128, 5, 152), (96, 32, 2, 304)])
+def test_tma_tile_cursor_matches_division(Sg, TS, outer, grid):
+    """A CTA takes a contiguous run of tiles; the copy thread walks it with an incremental
+    cursor (column tile xt, row group yt) instead of dividing.  The cursor must give the
+    positions t % tpo, t / tpo of every tile, every tile must belong to exactly one CTA,
+    and the TMA x coordinate (xt TS floats) must be a multiple of 16 bytes."""
+    tpo = (Sg + TS - 1) // TS
+    ntiles = outer * tpo
+    per = (ntiles + grid - 1) // grid
+    seen = np.zeros(ntiles, dtype=np.int64)
+    for b in range(grid):
+        first = b * per
+        mine = min(per, ntiles - first) if first < ntiles else 0
+        xt, yt = first % tpo, first // tpo
+        for i in range(mine):
+            t = first + i
+            assert (xt, yt) == (t % tpo, t // tpo)
+            assert (xt * TS * 4) % 16 == 0
+            seen[t] += 1
+            xt += 1
+            if xt == tpo:
+                xt, yt = 0, yt + 1
+    assert np.all(seen == 1)
+
+
+def items_of(I, st, Pg, R):
+    """(fibre start, first output) of each work item of one mode, as item_geometry."""
+    nfib = Pg // I
+    out = []
+    for it in range(((I + R - 1) // R) * nfib):
+        ch, fiber = it // nfib, it % nfib
+        out.append((fiber % st + st * I * (fiber // st), ch * R))
+    return out
+
+
+@pytest.mark.parametrize("modes", [(16, 16), (8,), (3, 32), (5, 3), (16,), (2, 4), (32,)])
+@pytest.mark.parametrize("TS,R", [(32, 8), (128, 8), (256, 8), (32, 2), (256, 2)])
+def test_transform_items_cover_the_tile_once(modes, TS, R):
+    """The work items of each mode of a pass cover every (fibre, output) row of the tile
+    exactly once and stay inside its Pg rows; when a mode has at most one item per row
+    slot (the case the TMA kernel computes once per thread), thread row slot rs holds
+    item rs, which is what the general loop gives it first."""
+    Pg = int(np.prod(modes))
+    nrs = KTHREADS // (TS // 4)
+    st = 1
+    for I in modes:
+        rows = np.zeros(Pg, dtype=np.int64)
+        for fbase, j0 in items_of(I, st, Pg, R):
+            for r in range(R):
+                if j0 + r < I:
+                    row = fbase + st * (j0 + r)
+                    assert 0 <= row < Pg
+                    rows[row] += 1
+        assert np.all(rows == 1)
+        items = len(items_of(I, st, Pg, R))
+        if items <= nrs:
+            general = {rs: items_of(I, st, Pg, R)[rs] for rs in range(nrs) if rs < items}
+            assert len(general) == items
+        st *= I
+
+
+@pytest.mark.parametrize("G,E", [(16, 7), (16, 9), (8, 18), (16, 16), (32, 18), (16, 4)])
+def test_fp32_register_pairs_cover_rows_once(G, E):
+    """FP32 block sweeps hold a column's rows in adjacent pairs: lane l takes rows
+    2 l + 2 G k and the next (k < E / 2) and, for odd E, row 2 G (E / 2) + l.  Together the
+    G lanes must hold rows 0 .. G E - 1 once each, and every pair must start on an even
+    row (8-byte loads; the leading dimension is even)."""
+    EP = E // 2
+    rows = np.zeros(G * E, dtype=np.int64)
+    for lane in range(G):
+        for k in range(EP):
+            r0 = 2 * lane + 2 * G * k
+            assert r0 % 2 == 0
+            rows[r0] += 1
+            rows[r0 + 1] += 1
+        if E % 2:
+            rows[2 * G * EP + lane] += 1
+    assert np.all(rows == 1)
+
+
+def pivot_key(s, c):
+    """The QR pivot key of column c with squared norm s (high 32 bits of the value's
+    bit pattern above the inverted index), as in lt_jacobi_svt.cuh."""
+    if s.dtype == np.float32:
+        hi = int(np.array(s, dtype=np.float32).view(np.uint32))
+    else:
+        hi = int(np.array(s, dtype=np.float64).view(np.uint64)) >> 32
+    return (hi << 32) | (0xFFFFFFFF - c)
+
+
+def pivot_index(key):
+    return 0xFFFFFFFF - (key & 0xFFFFFFFF)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_pivot_key_picks_largest_norm_then_smallest_index(dt):
+    """The maximum of the keys names the column of largest squared norm and, among equal
+    keys, the smallest index: non-negative floats order like their bit patterns."""
+    rng = np.random.default_rng(7)
+    for trial in range(200):
+        n = int(rng.integers(1, 300))
+        s = (rng.random(n) * 10.0 ** rng.integers(-30, 30)).astype(dt)
+        if trial % 3 == 0:
+            s[rng.integers(0, n, size=max(1, n // 4))] = s.max()  # ties at the maximum
+        if trial % 7 == 0:
+            s[:] = 0  # all columns exhausted
+        p = pivot_index(max(pivot_key(s[c], c) for c in range(n)))
+        if dt is np.float32:
+            assert s[p] == s.max() and p == int(np.flatnonzero(s == s.max())[0])
+        else:  # the key keeps the high 32 bits: a relative tie band of 2^-20
+            assert s[p] >= s.max() * (1 - 2.0 ** -19)
+            best = max(int(np.array(v).view(np.uint64)) >> 32 for v in s)
+            cand = [c for c in range(n) if int(np.array(s[c]).view(np.uint64)) >> 32 == best]
+            assert p == cand[0]
